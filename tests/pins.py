@@ -1,0 +1,147 @@
+"""Pins of the oracle: each returns a discrepancy that is at rounding level
+for a correct oracle.  They take the oracle module as an argument so that a
+test can plant a mistake in it (on the CPU) and check the pin catches it.
+
+What each pin rests on (none of them re-types the oracle's formulas):
+  operator_vs_bruteforce  Eq. (2.3) integrated in a different parametrisation
+  rj_zero                 Eq. (2.6): the bracket vanishes on Rayleigh-Jeans states
+  weight_total            sum_p W_p = |S^{d-1}|^2 R^{2d-2}/(2d-2), closed form
+  fast_vs_realspace       band-limited f: spectral interpolation is exact
+  fast_vs_direct          the FFT route equals the O(N^{3d}) sums (3.3)-(3.6)
+  alg1_vs_fast            Algorithm 1 literally vs its linearity-reduced form
+  mass_bandlimited        Appendix B's symmetry argument (sum_i Q_i = 0)
+  naive_dft               Eq. (3.1) summed term by term
+"""
+import math
+
+import numpy as np
+
+import wke_inputs as I
+from tests import bruteforce_eq23 as BF
+
+L = 8.0
+
+
+def _gauss(k):
+    return np.exp(-0.5 * np.sum(np.asarray(k) ** 2, axis=-1))
+
+
+def operator_vs_bruteforce(O, d):
+    """Relative difference between the oracle's Eq. (2.7) quadrature (many
+    nodes, R large enough that truncation is negligible) and the direct
+    integral of Eq. (2.3), for a Gaussian f at a few points."""
+    if d == 2:
+        quad = O.make_quadrature(2, 64, 64, 64, 14.0, "midpoint")
+        pts = [[0.3, -0.5], [1.2, 0.4]]
+        ref = [BF.collision_2d(_gauss, p) for p in pts]
+    else:
+        quad = O.make_quadrature(3, 40, 128, 128, 14.0, "product:8:16")
+        pts = [[0.3, -0.5, 0.2]]
+        ref = [BF.collision_3d(_gauss, p) for p in pts]
+    got = O.collision_realspace(_gauss, np.array(pts), quad)
+    ref = np.array(ref)
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+def rj_zero(O, d):
+    """max |Q| / max |K1| on Rayleigh-Jeans states for the real-space form
+    (any quadrature): the per-node bracket is identically zero."""
+    worst = 0.0
+    for mu, nu, xi in [(1.0, [0.3, -0.2, 0.1], 0.1), (50.0, [5.0, 5.0, 0.0], 100.0)]:
+        if d == 2:
+            quad = O.make_quadrature(2, 6, 5, 5, O.default_R(L), "midpoint")
+        else:
+            quad = O.make_quadrature(3, 4, 8, 6, O.default_R(L), "cube", "octahedron")
+        fn = I.rayleigh_jeans_fn(d, mu, nu[:d], xi)
+        k = O.grid_points(d, 6, L).reshape(-1, d)
+        q = O.collision_realspace(fn, k, quad)
+        gain = np.zeros(len(k))
+        F = fn(k)
+        for _p1, _p2, _p3, W, c, a, b in quad.nodes():
+            gain += W * np.abs(fn(k - a) * fn(k - b) * fn(k - c))
+        worst = max(worst, float(np.max(np.abs(q)) / np.max(gain * 2.0 ** (1 - d))))
+        del F
+    return worst
+
+
+def weight_total(O, d):
+    """Relative error of sum_p W_p against |S^{d-1}|^2 R^{2d-2}/(2d-2)."""
+    R = 5.5
+    if d == 2:
+        quad = O.make_quadrature(2, 5, 7, 3, R, "midpoint")
+        area = 2.0 * math.pi
+    else:
+        quad = O.make_quadrature(3, 5, 12, 20, R, "icosahedron", "dodecahedron")
+        area = 4.0 * math.pi
+    tot = sum(n[3] for n in quad.nodes())
+    exact = area * area * R ** (2 * d - 2) / (2 * d - 2)
+    return abs(tot - exact) / exact
+
+
+def fast_vs_realspace(O, d):
+    """Band-limited f (|j_c| <= 3 < N/2): the fast form on the grid equals
+    the real-space form with the exact f.  The rules are neither antipodal
+    nor symmetric under coordinate swaps, so a sign or axis mix-up in the
+    shifts cannot cancel between nodes."""
+    if d == 2:
+        N, quad = 16, O.make_quadrature(2, 6, 3, 5, O.default_R(L), "midpoint")
+    else:
+        N, quad = 8, O.make_quadrature(3, 3, 6, 6, O.default_R(L), "product:2:3", "octahedron")
+    tp = I.trig_poly(d, L, 3, 6, 11)
+    qf, _ = O.collision_fast(tp.on_grid(N), L, quad)
+    qr = O.collision_realspace(tp, O.grid_points(d, N, L), quad)
+    return float(np.max(np.abs(qf - qr)) / np.max(np.abs(qr)))
+
+
+def fast_vs_direct(O, d, N=None, quad=None, f=None):
+    """The FFT route against the classical sums with quadrature weights and
+    circular index wrap (the sums N-point transforms compute).  Default rules
+    are not antipodal, so A and B (k' and k2') cannot trade places unseen."""
+    if quad is None:
+        if d == 2:
+            N, quad = 8, O.make_quadrature(2, 4, 4, 3, O.default_R(L), "midpoint")
+        else:
+            N, quad = 4, O.make_quadrature(3, 2, 8, 6, O.default_R(L), "cube", "product:2:3")
+    if f is None:
+        f = I.gaussian_noise(d, N, L, 99, eps=0.2) * I.gaussian(d, N, L, 1.3)
+    qf, imf = O.collision_fast(f, L, quad)
+    qd, imd = O.collision_direct(f, L, quad, wrap=True)
+    return float(np.max(np.abs(qf - qd)) / np.max(np.abs(qd)))
+
+
+def alg1_vs_fast(O, d):
+    if d == 2:
+        N, quad = 8, O.make_quadrature(2, 3, 4, 4, O.default_R(L), "midpoint")
+    else:
+        N, quad = 4, O.make_quadrature(3, 2, 6, 8, O.default_R(L), "octahedron", "cube")
+    f = I.gaussian_noise(d, N, L, 5, eps=0.3)
+    qa, _ = O.collision_alg1(f, L, quad)
+    qf, _ = O.collision_fast(f, L, quad)
+    return float(np.max(np.abs(qa - qf)) / np.max(np.abs(qf)))
+
+
+def mass_bandlimited(O, d):
+    """|sum_i Q_i| / sum_i |Q_i| for f with |j_c| <= N/3 - 1 and the same
+    antipodal rule for qhat and sigma (Appendix B's symmetry argument)."""
+    if d == 2:
+        N, quad = 18, O.make_quadrature(2, 5, 6, 6, O.default_R(L), "midpoint")
+    else:
+        N, quad = 12, O.make_quadrature(3, 3, 8, 8, O.default_R(L), "cube")
+    tp = I.trig_poly(d, L, N // 3 - 1, 8, 3)
+    q, _ = O.collision_fast(tp.on_grid(N), L, quad)
+    return float(abs(np.sum(q)) / np.sum(np.abs(q)))
+
+
+def naive_dft(O, d):
+    """FFT/iFFT against Eq. (3.1) summed term by term."""
+    N = 6 if d == 2 else 4
+    g = I.gaussian_noise(d, N, L, 17, eps=0.5)
+    k = O.grid_points(d, N, L).reshape(-1, d)
+    j = O.mode_vectors(d, N).reshape(-1, d)
+    E = np.exp(-1j * math.pi / L * (j @ k.T))              # (modes, points)
+    ref_hat = (E @ g.reshape(-1)) / N ** d
+    got_hat = O.FFT(g, L).reshape(-1)
+    back = O.iFFT(O.FFT(g, L), L).reshape(-1)
+    ref_back = np.conj(E).T @ ref_hat
+    return float(max(np.max(np.abs(got_hat - ref_hat)), np.max(np.abs(back - ref_back)),
+                     np.max(np.abs(ref_back - g.reshape(-1)))))
