@@ -1,0 +1,361 @@
+"""Benchmark: collision-operator evaluations per second on one GB300.
+
+A step is one evaluation of Q(f) (the whole hot path: forward transform,
+phase-weighted spectra and inverse transforms of every shifted field, cubic
+products, accumulation over all M quadrature nodes) on the 3D N=64, M=2048
+workload (32 radial x 8 x 8 cube directions, ring f = exp(-(|k|-3)^2), L=8).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is FP32 evaluations/s with f resident on the
+device; `e2e` is the same through the host-buffer C-ABI call with the copies
+inside the timed region.  L2 is flushed (256 MiB write) before every timed
+step; per-step times come from CUDA events on the launching stream.  The
+reference arm times the CPU FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import wke_inputs as I  # noqa: E402
+
+METRIC = "Q(f) evals/s at 3D N=64 (FP32/split vs FP64 GPU, ≤1e-6 rel); serving p50/p99 ms"
+UNIT = "evals/s"
+WORKLOAD = I.WORKLOADS["3d_n64_m2048"]
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def _config(precision="fp32"):
+    w = WORKLOAD
+    return {"workload": f"{w.name}: 3D N={w.N}, L={w.L}, M={w.M} ({w.n_r} radial x {w.n_s} x {w.n_sig} "
+                        f"{w.sphere} directions), ring f=exp(-(|k|-3)^2), Nyquist kept",
+            "d": w.d, "N": w.N, "M": w.M, "precision": precision,
+            "l2": "flushed before every timed step (256 MiB write, outside the step events)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _oracle_chunk(args):
+    lo, hi = args
+    import numpy as np  # noqa: F401
+    from oracle import wke_oracle as O
+    w = WORKLOAD
+    quad = O.make_quadrature(w.d, w.n_r, w.n_s, w.n_sig, O.default_R(w.L), w.sphere)
+    t = time.perf_counter()
+    O.collision_fast(w.initial(), w.L, quad, node_range=(lo, hi))
+    return time.perf_counter() - t
+
+
+def cpu_oracle_rate(pool, nodes_per_worker, workers):
+    """Evaluations/s of the FP64 oracle on `workers` host processes, from a
+    bounded sample: each worker sums `nodes_per_worker` nodes of the workload."""
+    w = WORKLOAD
+    group = w.n_sig
+    ranges = []
+    for k in range(workers):
+        lo = (k * nodes_per_worker // group) * group % w.M
+        ranges.append((lo, min(w.M, lo + nodes_per_worker)))
+    t = time.perf_counter()
+    list(pool.map(_oracle_chunk, ranges))
+    wall = time.perf_counter() - t
+    nodes = sum(h - l for l, h in ranges)
+    return (nodes / w.M) / wall, wall, nodes
+
+
+def make_pool():
+    import multiprocessing as mp
+    workers = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(workers), workers
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def _measured_peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args, rank, world, pool, workers):
+    import numpy as np
+    import torch
+    from paper_2503_12805_gb300 import wke
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    f64 = w.initial()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make(prec):
+        return wke.Plan(w.d, w.N, w.L, w.n_r, w.n_s, w.n_sig, sphere=w.sphere, precision=prec)
+
+    def timed(plan, f, Q, steps, warmup, profile=False):
+        for _ in range(warmup):
+            plan.collision(f, Q)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            wke.wke_plan_profile(plan.handle, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)                    # evict L2 between steps
+            ev[i][0].record(stream)
+            plan.collision(f, Q)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = None
+        if profile:
+            prof = wke.wke_plan_profile_read(plan.handle)
+            wke.wke_plan_profile(plan.handle, False)
+        if world > 1:
+            torch.distributed.barrier()
+        return ms, wall, prof
+
+    # FP32 headline
+    p32 = make("fp32")
+    info = p32.info()
+    f32 = torch.tensor(f64, dtype=torch.float32, device=dev)
+    Q32 = torch.empty_like(f32)
+    with ClockSampler(dev.index) as clk:
+        ms32, wall32, prof = timed(p32, f32, Q32, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    t_step = sum(ms32) / len(ms32)
+    t_max = t_step
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * 1000.0 / t_max
+
+    # FP64 path on the same GPU (fewer steps: it is far slower)
+    p64 = make("fp64")
+    fd = torch.tensor(f64, dtype=torch.float64, device=dev)
+    Q64 = torch.empty_like(fd)
+    ms64, _, _ = timed(p64, fd, Q64, max(2, min(args.steps, 5)), max(1, min(args.warmup, 2)))
+    fp64_rate = 1000.0 / (sum(ms64) / len(ms64))
+    q32 = Q32.double().cpu().numpy()
+    q64 = Q64.cpu().numpy()
+    rel_err = float(np.max(np.abs(q32 - q64)) / np.max(np.abs(q64)))
+
+    # end to end through the host-buffer call
+    fh = torch.tensor(f64, dtype=torch.float32).pin_memory()
+    qh = torch.empty_like(fh).pin_memory()
+    wke.wke_plan_set_stream(p32.handle, stream.cuda_stream)
+    for _ in range(max(1, args.warmup)):
+        p32.collision_host(fh, qh)
+    e2e_steps = args.steps
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p32.collision_host(fh, qh)
+    e2e_rate = world * e2e_steps / (time.perf_counter() - t0)
+
+    # roofline of the dominant kernel class
+    peaks = _measured_peaks()
+    classes = {c: v for c, v in prof.items() if v[1] > 0}
+    dom = max(classes, key=lambda c: classes[c][0])
+    dom_ms, dom_n = classes[dom]
+    per_launch_ms = dom_ms / dom_n
+    flops_launch = kernel_flops(dom, info)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
+                "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "per_launch_ms": round(per_launch_ms, 5), "launches": dom_n,
+                "kernel_share": {c: round(v[0] / sum(x[0] for x in classes.values()), 4)
+                                 for c, v in classes.items()}}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config("fp32"),
+        "parallelism": "replicas" if world > 1 else "single-gpu",
+        "fp64_evals_per_s": round(fp64_rate, 4), "speedup_fp32_vs_fp64": round(value / world / fp64_rate, 2),
+        "fp32_rel_err_vs_fp64_gpu": rel_err, "wall_s_timed": round(wall32, 4),
+        "e2e": {"value": round(e2e_rate, 3), "unit": UNIT, "h2d_bytes_per_step": fh.numel() * 4,
+                "d2h_bytes_per_step": qh.numel() * 4},
+        "gpu_launches": args.steps * info.launches_per_collision,
+        "clocks": clocks, "roofline": roofline,
+        "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
+                 "fields_per_group": info.fields_per_group, "products_per_group": info.products_per_group,
+                 "flops_per_eval": info.flops_per_collision, "l2_bytes_per_eval": info.l2_bytes_per_collision},
+    }
+    if rank == 0 and pool is not None:
+        rate, wall, nodes = cpu_oracle_rate(pool, args.oracle_nodes, workers)
+        line["cpu_baseline"] = {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
+                                "sample": f"{nodes} of {w.M} nodes of one evaluation ({args.oracle_nodes} per "
+                                          f"process, {workers} spawn processes, {wall:.1f} s wall), scaled to "
+                                          "full evaluations"}
+    p32.close()
+    p64.close()
+    return line
+
+
+def kernel_flops(cls, info):
+    """Algorithmic flops of one launch of a kernel class (the arithmetic the
+    executed algorithm needs: 5 n log2 n per complex n-point transform, two
+    complex products per point for the phases, 30 per point per product)."""
+    d, N, G = info.d, info.N, info.groups_per_chunk
+    nd = N ** d
+    P = nd // N
+    fpg, ppg = info.fields_per_group, info.products_per_group
+    if cls == "pass1":
+        per_field = N * (5.0 * P * math.log2(P) + 12.0 * P)
+        return G * fpg * per_field
+    if cls == "pass2":
+        per_group = (1 + 2 * ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
+        return G * per_group
+    if cls == "forward":
+        return 5.0 * nd * math.log2(nd)
+    return 2.0 * G * nd
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    pool, workers = make_pool()
+    try:
+        rates = []
+        t0 = time.perf_counter()
+        for _ in range(args.warmup):
+            cpu_oracle_rate(pool, max(8, args.oracle_nodes // 4), workers)
+        for _ in range(args.steps):
+            rates.append(cpu_oracle_rate(pool, args.oracle_nodes, workers)[0])
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+    rate = statistics.median(rates)
+    return {"impl": "reference", "metric": METRIC, "value": round(rate, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / rate, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config("fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"{args.oracle_nodes} nodes per process per step, {workers} spawn "
+                                       f"processes, scaled to full evaluations; {wall:.1f} s wall"},
+            "e2e": {"value": round(rate, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--oracle-nodes", type=int, default=16,
+                    help="oracle nodes per host process per sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    # the oracle's process pool starts before the first GPU call
+    pool, workers = (None, 0)
+    if rank == 0 and not args.no_cpu_baseline:
+        pool, workers = make_pool()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    try:
+        line = run_gpu(args, rank, world, pool, workers)
+    finally:
+        if pool is not None:
+            pool.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

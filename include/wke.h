@@ -1,0 +1,208 @@
+/*
+ * wke.h -- C ABI of the GB300 (sm_103a) collision-operator library.
+ *
+ * The library evaluates the collision operator of the 4-wave kinetic equation
+ * with omega(k) = |k|^2/2 (or |k|^2, see dispersion) and beta = 0, in the
+ * Boltzmann-type spherical form of Qi, Shen and Wang, "A fast Fourier
+ * spectral method for wave kinetic equation" (arXiv 2503.12805),
+ * Eq. (2.7)-(2.8), discretised as in Sec. 3:
+ *
+ *   Q(k_i) = 2^{1-d} sum_p W_p [ A B (C + F) - C F (A + B) ](k_i)
+ *
+ * on the periodic grid k_i = -L + i 2L/N of D_L = [-L, L]^d (Sec. 3.2,
+ * Step 1), where for every quadrature node p = (p1, p2, p3) of Eq. (3.8)
+ *   F = f(k_i), C = f_N(k_i - q), A = f_N(k_i - a), B = f_N(k_i - b),
+ *   q = |q|_{p1} qhat_{p2}, a = (q - |q| sigma_{p3})/2, b = (q + |q| sigma_{p3})/2,
+ *   W_p = w_r |q|_{p1}^{2d-3} w_s w_sig,
+ * f_N the truncated Fourier series of Eq. (3.1) with modes [-N/2, N/2-1]^d.
+ * The four products are the terms K1 = ABC, K2 = FCB, K3 = AFB, K4 = ACF of
+ * Eq. (2.7); Algorithm 1 (Sec. 3.4) computes the same sum with its forward
+ * and inverse transforms of each product cancelled by linearity.  The
+ * Nyquist modes -N/2 are kept by default, so shifted fields are complex:
+ * Q is returned as its real part, the imaginary part on request.
+ *
+ * Conventions for every call below:
+ *   - Grids are N^d arrays in row-major order (last axis fastest), in the
+ *     plan's precision: double for WKE_FP64, float for WKE_FP32.
+ *   - Pointers named *_dev are device pointers (cudaMalloc or torch CUDA
+ *     memory) owned by the caller; *_host are host pointers owned by the
+ *     caller.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls taking a stream are asynchronous on it and do not
+ *     synchronise the host unless stated.
+ *   - Every call returns WKE_OK (0) or a negative WKE_ERR_* code; it never
+ *     aborts or throws.  wke_last_error_string() describes the last failure
+ *     on the calling thread.
+ *   - A plan may be used by one host thread at a time.
+ */
+#ifndef WKE_H
+#define WKE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define WKE_OK                 0
+#define WKE_ERR_INVALID       -1   /* bad argument (sizes, rule, pointers)   */
+#define WKE_ERR_OOM           -2   /* device or host allocation failed        */
+#define WKE_ERR_CUDA          -3   /* a CUDA runtime call or launch failed    */
+#define WKE_ERR_UNSUPPORTED   -4   /* valid request this build does not serve */
+
+/* ------------------------------------------------------------ enumerations */
+/* Sphere rules (Sec. 3.3: mid-point in 2D, spherical designs in 3D). */
+#define WKE_SPHERE_MIDPOINT_2D  0  /* theta_p = (p + 1/2) 2pi/n, weight 2pi/n  */
+#define WKE_SPHERE_PLATONIC_3D  1  /* n = 6, 8, 12, 20 vertex designs, 4pi/n   */
+#define WKE_SPHERE_PRODUCT_3D   2  /* Gauss-Legendre in cos(theta) x mid-point
+                                      in phi; n_theta = *_param, n_phi = n/n_theta */
+#define WKE_SPHERE_USER         3  /* caller's directions and weights          */
+
+#define WKE_FP64  0   /* every step in double                                 */
+#define WKE_FP32  1   /* transforms and products in float, tables computed in
+                         double and rounded, forward transform and the sum over
+                         quadrature groups in double                           */
+
+#define WKE_NYQ_KEEP  0   /* modes [-N/2, N/2-1]^d as in Eq. (3.1) (default)  */
+#define WKE_NYQ_ZERO  1   /* zero every mode with a component equal to -N/2   */
+
+#define WKE_OMEGA_HALF_K2  0   /* omega = |k|^2/2, the paper's numerics (Sec. 2) */
+#define WKE_OMEGA_K2       1   /* omega = |k|^2: the frequency delta halves Q    */
+
+/* Quadrature and numerics of a plan (Eq. (3.8)).  Fill with
+ * wke_quadrature_default() and then override fields. */
+typedef struct wke_quadrature {
+    int n_r;                 /* radial Gauss-Legendre nodes on [0, R]          */
+    int n_s;                 /* directions qhat                                */
+    int n_sig;               /* collision angles sigma                         */
+    int sphere_rule;         /* rule for qhat (WKE_SPHERE_*)                   */
+    int sphere_rule_sig;     /* rule for sigma; -1 = same as sphere_rule       */
+    int sphere_param;        /* n_theta of WKE_SPHERE_PRODUCT_3D for qhat      */
+    int sphere_param_sig;    /* n_theta for sigma                              */
+    const double *user_s;    /* WKE_SPHERE_USER: n_s rows of (d coords, weight)
+                                for qhat, host memory, read at plan creation   */
+    const double *user_sig;  /* same for sigma                                 */
+    double R;                /* radial cut-off; 0 => R = 4L/(3 + sqrt 2), i.e.
+                                R = 2S with L = (3 + sqrt 2) S / 2 (Step 1)     */
+    int precision;           /* WKE_FP64 or WKE_FP32                           */
+    int nyquist;             /* WKE_NYQ_KEEP or WKE_NYQ_ZERO                   */
+    int dispersion;          /* WKE_OMEGA_HALF_K2 or WKE_OMEGA_K2              */
+    int pair_antipodal;      /* 1 (default): when the sigma rule is antipodal
+                                with equal weights, evaluate the identical
+                                fields f_N(k - b(sigma)) = f_N(k - a(-sigma))
+                                and the identical node products once; 0: every
+                                node separately, as Algorithm 1 loops          */
+    size_t chunk_bytes;      /* budget for the per-chunk intermediate fields;
+                                0 => 48 MiB (sized to stay resident in L2)     */
+} wke_quadrature;
+
+typedef struct wke_plan wke_plan;   /* opaque */
+
+/* Counts describing a plan (for tests, benchmarks and admission). */
+typedef struct wke_plan_info {
+    int d, N, M, precision;
+    int n_groups;            /* n_r * n_s: nodes sharing C = f_N(k - q)       */
+    int fields_per_group;    /* distinct shifted fields per group             */
+    int products_per_group;  /* distinct node products per group              */
+    int groups_per_chunk;
+    int n_chunks;
+    int launches_per_collision;  /* kernels one wke_collision launches        */
+    double flops_per_collision;  /* arithmetic of the transforms, phases and
+                                    products actually executed (5 n log2 n per
+                                    complex transform of n points)            */
+    double l2_bytes_per_collision; /* intermediate-field traffic (write + read)*/
+    size_t device_bytes;     /* device memory the plan owns                    */
+} wke_plan_info;
+
+/* ------------------------------------------------------------ calls */
+
+/* Defaults: 2D mid-point / 3D cube rules, R = 0 (automatic), FP64, Nyquist
+ * kept, omega = |k|^2/2, antipodal pairing on, 48 MiB chunks.  n_r, n_s,
+ * n_sig are set to 0 and must be filled in.  Returns WKE_ERR_INVALID if q is
+ * NULL. */
+int wke_quadrature_default(wke_quadrature *q);
+
+/* Create a plan for d in {2, 3}, N a power of two (16..256 in 2D, 16..64 in
+ * 3D), half-width L > 0, and M = n_r * n_s * n_sig quadrature nodes
+ * (Algorithm 1 inputs: grid size, N_r, N_s, N_sig, nodes and weights).
+ * Builds the nodes, weights and shift vectors, the per-axis phase tables
+ * exp(-i pi j x / L) and transform twiddles in double precision on the host
+ * and uploads them, and allocates all device workspace on the current CUDA
+ * device.  *out receives the plan (NULL on failure).
+ * Errors: WKE_ERR_INVALID (d, N, L, M or the rule out of range, M !=
+ * n_r n_s n_sig, unknown Platonic size, user rule with zero-length
+ * direction), WKE_ERR_UNSUPPORTED (valid N without a compiled kernel),
+ * WKE_ERR_OOM, WKE_ERR_CUDA. */
+int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad,
+                    wke_plan **out);
+
+/* Release the plan's device memory and host state.  NULL is accepted.  The
+ * caller must ensure no work using the plan is still running. */
+int wke_plan_destroy(wke_plan *plan);
+
+/* Device bytes a plan with these parameters would own, without creating it
+ * (admission control).  Errors as wke_plan_create, minus OOM/CUDA. */
+int wke_plan_footprint_bytes(int d, int N, double L, int M,
+                             const wke_quadrature *quad, size_t *bytes);
+
+/* Fill *info for an existing plan. */
+int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info);
+
+/* Copy the node table to host memory: M rows, in (p1, p2, p3) lexicographic
+ * order, of 1 + 3d doubles: W_p, q (d), a (d), b (d).  `out_host` must hold
+ * M * (1 + 3d) doubles. */
+int wke_plan_node_table(const wke_plan *plan, double *out_host);
+
+/* Q = Re K(f) on the grid (Eq. (2.7) discretised as above; Algorithm 1's
+ * output).  f_dev: N^d values, read only.  Q_dev: N^d values, written.  They
+ * must not overlap.  Asynchronous on `stream`; the plan's workspace is in use
+ * until the stream reaches the end of the call, so calls with one plan on
+ * different streams must be ordered by the caller. */
+int wke_collision(wke_plan *plan, const void *f_dev, void *Q_dev, void *stream);
+
+/* As wke_collision and, if Qim_dev is not NULL, also Im K(f) into Qim_dev
+ * (N^d values, plan precision): nonzero only through the kept Nyquist modes. */
+int wke_collision_ex(wke_plan *plan, const void *f_dev, void *Q_dev, void *Qim_dev,
+                     void *stream);
+
+/* End-to-end variant with host buffers: copies f_host to plan-owned device
+ * memory, evaluates, copies Q back to Q_host and synchronises the plan's
+ * stream before returning.  Pinned host memory gives full copy bandwidth. */
+int wke_collision_host(wke_plan *plan, const void *f_host, void *Q_host);
+
+/* Stream used by wke_step and wke_collision_host (default: NULL). */
+int wke_plan_set_stream(wke_plan *plan, void *stream);
+
+/* One explicit Runge-Kutta step of df/dt = Q(f) on the grid values (the
+ * paper integrates with RK4, Sec. 4): rk_stages 1 = forward Euler, 2 = Heun,
+ * 4 = classical RK4.  f_dev is updated in place on the plan's stream;
+ * asynchronous.  Errors: WKE_ERR_INVALID for other rk_stages or dt not finite. */
+int wke_step(wke_plan *plan, void *f_dev, double dt, int rk_stages);
+
+/* Macroscopic moments of a grid function g (Sec. 2): out_dev[0] = h^d sum g
+ * (mass), out_dev[1..d] = h^d sum k g (momentum), out_dev[d+1] = h^d sum
+ * |k|^2 g (energy), h = 2L/N, summed in double in a fixed order.  out_dev is
+ * a device pointer to d + 2 doubles.  Asynchronous on `stream`. */
+int wke_moments(wke_plan *plan, const void *g_dev, double *out_dev, void *stream);
+
+/* Kernel timing.  While enabled, every wke_collision records CUDA events
+ * around its launches on the call's stream (no host synchronisation).
+ * wke_plan_profile_read() must be called after that stream is idle: it adds
+ * up the recorded intervals per kernel class into out_host[2 * WKE_PROF_CLASSES]
+ * as (total milliseconds, number of launches) pairs, in the order forward,
+ * pass 1, pass 2, finalize, and forgets them.  Enabling resets the record. */
+#define WKE_PROF_CLASSES 4
+int wke_plan_profile(wke_plan *plan, int enable);
+int wke_plan_profile_read(wke_plan *plan, double *out_host);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *wke_last_error_string(void);
+
+/* Library version string. */
+const char *wke_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WKE_H */

@@ -313,7 +313,7 @@ def shifted_field(fhat: np.ndarray, L: float, x: np.ndarray) -> np.ndarray:
 
 
 def collision_fast(f: np.ndarray, L: float, quad: Quadrature, nyquist: str = "keep",
-                   node_range: tuple[int, int] | None = None):
+                   node_range: tuple[int, int] | None = None, return_complex: bool = False):
     """Algorithm 1 with its transform pairs cancelled by linearity.
 
     Per node, on the grid: F = f(k_i), C = f_N(k_i - q) [= f(k2)],
@@ -324,7 +324,7 @@ def collision_fast(f: np.ndarray, L: float, quad: Quadrature, nyquist: str = "ke
     identity on [-N/2, N/2-1]^d, so this equals ``collision_alg1`` up to
     rounding.  ``node_range`` restricts the sum to flat node indices
     [lo, hi) (lexicographic order) for timing samples.
-    Returns (Re Q, max |Im Q|)."""
+    Returns (Re Q, max |Im Q|), or the complex Q if ``return_complex``."""
     d, N = f.ndim, f.shape[0]
     fhat = _apply_nyquist(FFT(f, L), nyquist)
     F = f.astype(np.float64)
@@ -346,6 +346,8 @@ def collision_fast(f: np.ndarray, L: float, quad: Quadrature, nyquist: str = "ke
         K4 = A * C * F
         acc += W * (K1 - K2 + K3 - K4)
     Q = 2.0 ** (1 - d) * acc
+    if return_complex:
+        return Q
     return Q.real.copy(), float(np.max(np.abs(Q.imag)))
 
 

@@ -1,0 +1,442 @@
+// C ABI of the library (declared in include/wke.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "wke_internal.h"
+
+namespace wke {
+const char *last_error();
+
+template <typename T> int forward_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
+template <typename T> int pass1_T(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);
+template <typename T> int pass2_T(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);
+template <typename T> int finalize_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
+template <typename T> int moments_T(const HostPlan &, const void *, double *, double *, cudaStream_t);
+template <typename T>
+int rk_stage_T(const HostPlan &, const void *, const void *, double *, void *, double, double, int, cudaStream_t);
+template <typename T> int rk_final_T(const HostPlan &, void *, const double *, double, cudaStream_t);
+
+int moments_partials_count(const HostPlan &) { return 256; }
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return fail(WKE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace wke
+
+using namespace wke;
+
+struct wke_plan {
+    HostPlan hp;
+    DevicePtrs dp{};
+    std::vector<void *> allocs;
+    void *f_stage = nullptr, *Q_stage = nullptr;   // wke_collision_host buffers
+    void *rk_y = nullptr, *rk_k = nullptr;
+    double *rk_acc = nullptr;
+    double *mom_partials = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t bytes = 0;
+    bool dirty = false;   // accumulators may hold a partial sum after a failure
+    // kernel timing (wke_plan_profile): recorded (class, start, stop) events
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_class;       // class of each recorded interval
+};
+
+namespace {
+
+size_t grid_elems(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
+
+int dev_alloc(wke_plan *p, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? WKE_ERR_OOM : WKE_ERR_CUDA,
+                    std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                        cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*ptr);
+    p->bytes += bytes;
+    return WKE_OK;
+}
+
+void free_plan(wke_plan *p) {
+    for (void *ptr : p->allocs) cudaFree(ptr);
+    p->allocs.clear();
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    p->ev_pool.clear();
+    p->ev_used = 0;
+    p->ev_class.clear();
+}
+
+// Record one event of a timed interval (profiling only); returns false when
+// an event could not be created, in which case timing is silently skipped.
+bool prof_event(wke_plan *p, cudaStream_t s) {
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        p->ev_pool.push_back(e);
+    }
+    cudaEventRecord(p->ev_pool[p->ev_used++], s);
+    return true;
+}
+
+struct ProfScope {
+    wke_plan *p;
+    cudaStream_t s;
+    bool on;
+    ProfScope(wke_plan *p_, cudaStream_t s_, int cls) : p(p_), s(s_), on(p_->profiling) {
+        if (on) {
+            on = prof_event(p, s);
+            if (on) p->ev_class.push_back(cls);
+        }
+    }
+    ~ProfScope() {
+        if (on && !prof_event(p, s)) {
+            // keep the pool consistent: drop the unmatched start
+            --p->ev_used;
+            p->ev_class.pop_back();
+        }
+    }
+};
+
+template <typename T> int upload_tables(wke_plan *p) {
+    const HostPlan &hp = p->hp;
+    typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type C;
+    const int nf = hp.n_groups * hp.fields_per_group;
+    std::vector<C> phase((size_t)nf * hp.d * hp.N);
+    std::vector<double> row(2 * hp.N);
+    for (int f = 0; f < nf; ++f)
+        for (int a = 0; a < hp.d; ++a) {
+            phase_row(hp.N, hp.L, hp.field_shift[(size_t)f * hp.d + a], row.data());
+            for (int k = 0; k < hp.N; ++k) {
+                C c;
+                c.x = (T)row[2 * k];
+                c.y = (T)row[2 * k + 1];
+                phase[((size_t)f * hp.d + a) * hp.N + k] = c;
+            }
+        }
+    std::vector<C> tw(hp.N);
+    std::vector<double2> tw64(hp.N);
+    const double two_pi = 6.28318530717958647692528676655900577;
+    for (int k = 0; k < hp.N; ++k) {
+        const double th = two_pi * k / hp.N;
+        tw64[k] = make_double2(std::cos(th), std::sin(th));
+        tw[k].x = (T)tw64[k].x;
+        tw[k].y = (T)tw64[k].y;
+    }
+    std::vector<int> pl(2 * hp.products_per_group);
+    for (int i = 0; i < hp.products_per_group; ++i) {
+        pl[2 * i] = hp.prod_fa[i];
+        pl[2 * i + 1] = hp.prod_fb[i];
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpy(const_cast<void *>(p->dp.phase), phase.data(), phase.size() * sizeof(C),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "phase table upload");
+    if ((e = cudaMemcpy(const_cast<void *>(p->dp.tw), tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "twiddle upload");
+    if ((e = cudaMemcpy(const_cast<double *>(p->dp.tw64), tw64.data(), tw64.size() * sizeof(double2),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "twiddle upload");
+    if ((e = cudaMemcpy(const_cast<int *>(p->dp.prod_local), pl.data(), pl.size() * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "product table upload");
+    if ((e = cudaMemcpy(const_cast<double *>(p->dp.prod_W), hp.prod_W.data(), hp.prod_W.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "weight upload");
+    return WKE_OK;
+}
+
+int clear_accumulators(wke_plan *p, cudaStream_t s) {
+    const size_t acc = (size_t)p->hp.groups_per_chunk * grid_elems(p->hp) * sizeof(double);
+    cudaError_t e = cudaMemsetAsync(p->dp.Qacc, 0, acc, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->dp.Qacc_im, 0, acc, s);
+    if (e != cudaSuccess) return cuda_fail(e, "accumulator reset");
+    p->dirty = false;
+    return WKE_OK;
+}
+
+template <typename T> int collision_T(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t s) {
+    HostPlan &hp = p->hp;
+    p->dp.f = f;
+    int rc;
+    if (p->dirty && (rc = clear_accumulators(p, s))) return rc;
+    int e;
+    {
+        ProfScope ps(p, s, 0);
+        e = forward_T<T>(hp, p->dp, s);
+    }
+    for (int c = 0; c < hp.n_chunks && !e; ++c) {
+        const int g0 = c * hp.groups_per_chunk;
+        const int ng = std::min(hp.groups_per_chunk, hp.n_groups - g0);
+        {
+            ProfScope ps(p, s, 1);
+            e = pass1_T<T>(hp, p->dp, g0, ng, s);
+        }
+        if (!e) {
+            ProfScope ps(p, s, 2);
+            e = pass2_T<T>(hp, p->dp, g0, ng, Qim != nullptr, s);
+        }
+    }
+    if (!e) {
+        ProfScope ps(p, s, 3);
+        e = finalize_T<T>(hp, p->dp, Q, Qim, s);
+    }
+    if (e) {
+        p->dirty = true;
+        return cuda_fail((cudaError_t)e, "collision launch");
+    }
+    return WKE_OK;
+}
+
+int collision(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t s) {
+    return p->hp.precision == WKE_FP32 ? collision_T<float>(p, f, Q, Qim, s) : collision_T<double>(p, f, Q, Qim, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int wke_quadrature_default(wke_quadrature *q) {
+    if (!q) return fail(WKE_ERR_INVALID, "quadrature descriptor is NULL");
+    std::memset(q, 0, sizeof(*q));
+    q->sphere_rule = -1;
+    q->sphere_rule_sig = -1;
+    q->R = 0.0;
+    q->precision = WKE_FP64;
+    q->nyquist = WKE_NYQ_KEEP;
+    q->dispersion = WKE_OMEGA_HALF_K2;
+    q->pair_antipodal = 1;
+    q->chunk_bytes = 0;
+    return WKE_OK;
+}
+
+int wke_plan_footprint_bytes(int d, int N, double L, int M, const wke_quadrature *quad, size_t *bytes) {
+    if (!bytes) return fail(WKE_ERR_INVALID, "bytes is NULL");
+    HostPlan hp;
+    int rc = build_host_plan(d, N, L, M, quad, hp);
+    if (rc) return rc;
+    *bytes = plan_device_bytes(hp);
+    return WKE_OK;
+}
+
+int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, wke_plan **out) {
+    if (!out) return fail(WKE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    wke_plan *p = new (std::nothrow) wke_plan();
+    if (!p) return fail(WKE_ERR_OOM, "host allocation failed");
+    int rc = build_host_plan(d, N, L, M, quad, p->hp);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    cudaGetDevice(&p->device);
+    const HostPlan &hp = p->hp;
+    const size_t nd = grid_elems(hp);
+    const size_t tb = hp.precision == WKE_FP64 ? 8 : 4, cxb = 2 * tb;
+    const size_t nf = (size_t)hp.n_groups * hp.fields_per_group;
+    void *ptr;
+#define ALLOC(field, bytes)                                  \
+    do {                                                     \
+        if ((rc = dev_alloc(p, &ptr, (bytes)))) goto error;  \
+        field = static_cast<decltype(field)>(ptr);           \
+    } while (0)
+    ALLOC(p->dp.ghat, nd * cxb);
+    ALLOC(p->dp.H, std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
+    p->dp.fwd_tmp = p->dp.H;
+    ALLOC(p->dp.Qacc, (size_t)hp.groups_per_chunk * nd * 8);
+    ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
+    ALLOC(p->dp.phase, nf * hp.d * hp.N * cxb);
+    ALLOC(p->dp.tw, hp.N * cxb);
+    ALLOC(p->dp.tw64, hp.N * 16);
+    ALLOC(p->dp.prod_local, hp.products_per_group * 2 * sizeof(int));
+    ALLOC(p->dp.prod_W, (size_t)hp.n_groups * hp.products_per_group * 8);
+    ALLOC(p->f_stage, nd * tb);
+    ALLOC(p->Q_stage, nd * tb);
+    ALLOC(p->rk_y, nd * tb);
+    ALLOC(p->rk_k, nd * tb);
+    ALLOC(p->rk_acc, nd * 8);
+    ALLOC(p->mom_partials, (size_t)moments_partials_count(hp) * (hp.d + 2) * 8);
+#undef ALLOC
+    rc = hp.precision == WKE_FP32 ? upload_tables<float>(p) : upload_tables<double>(p);
+    if (rc) goto error;
+    if ((rc = clear_accumulators(p, nullptr))) goto error;
+    {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "plan set-up");
+            goto error;
+        }
+    }
+    *out = p;
+    return WKE_OK;
+error:
+    free_plan(p);
+    delete p;
+    return rc;
+}
+
+int wke_plan_destroy(wke_plan *plan) {
+    if (!plan) return WKE_OK;
+    free_plan(plan);
+    delete plan;
+    return WKE_OK;
+}
+
+int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
+    if (!plan || !info) return fail(WKE_ERR_INVALID, "plan or info is NULL");
+    const HostPlan &hp = plan->hp;
+    info->d = hp.d;
+    info->N = hp.N;
+    info->M = hp.M;
+    info->precision = hp.precision;
+    info->n_groups = hp.n_groups;
+    info->fields_per_group = hp.fields_per_group;
+    info->products_per_group = hp.products_per_group;
+    info->groups_per_chunk = hp.groups_per_chunk;
+    info->n_chunks = hp.n_chunks;
+    info->launches_per_collision = 2 + 2 * hp.n_chunks + 1;
+    info->flops_per_collision = plan_flops(hp);
+    info->l2_bytes_per_collision = plan_l2_bytes(hp);
+    info->device_bytes = plan->bytes;
+    return WKE_OK;
+}
+
+int wke_plan_node_table(const wke_plan *plan, double *out) {
+    if (!plan || !out) return fail(WKE_ERR_INVALID, "plan or output is NULL");
+    const HostPlan &hp = plan->hp;
+    const int d = hp.d;
+    for (int p = 0; p < hp.M; ++p) {
+        double *row = out + (size_t)p * (1 + 3 * d);
+        row[0] = hp.W[p];
+        for (int a = 0; a < d; ++a) {
+            row[1 + a] = hp.q[(size_t)p * d + a];
+            row[1 + d + a] = hp.a[(size_t)p * d + a];
+            row[1 + 2 * d + a] = hp.b[(size_t)p * d + a];
+        }
+    }
+    return WKE_OK;
+}
+
+int wke_collision_ex(wke_plan *plan, const void *f, void *Q, void *Qim, void *stream) {
+    if (!plan || !f || !Q) return fail(WKE_ERR_INVALID, "plan, f and Q must be non-NULL");
+    if (f == Q || (Qim && (Qim == Q || Qim == f))) return fail(WKE_ERR_INVALID, "f, Q and Qim must not alias");
+    return collision(plan, f, Q, Qim, static_cast<cudaStream_t>(stream));
+}
+
+int wke_collision(wke_plan *plan, const void *f, void *Q, void *stream) {
+    return wke_collision_ex(plan, f, Q, nullptr, stream);
+}
+
+int wke_collision_host(wke_plan *plan, const void *f_host, void *Q_host) {
+    if (!plan || !f_host || !Q_host) return fail(WKE_ERR_INVALID, "plan, f_host and Q_host must be non-NULL");
+    const size_t bytes = grid_elems(plan->hp) * (plan->hp.precision == WKE_FP64 ? 8 : 4);
+    cudaStream_t s = plan->stream;
+    cudaError_t e = cudaMemcpyAsync(plan->f_stage, f_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    int rc = collision(plan, plan->f_stage, plan->Q_stage, nullptr, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(Q_host, plan->Q_stage, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return WKE_OK;
+}
+
+int wke_plan_set_stream(wke_plan *plan, void *stream) {
+    if (!plan) return fail(WKE_ERR_INVALID, "plan is NULL");
+    plan->stream = static_cast<cudaStream_t>(stream);
+    return WKE_OK;
+}
+
+int wke_step(wke_plan *plan, void *f, double dt, int rk_stages) {
+    if (!plan || !f) return fail(WKE_ERR_INVALID, "plan and f must be non-NULL");
+    if (!std::isfinite(dt)) return fail(WKE_ERR_INVALID, "dt must be finite");
+    // Butcher tableaux: b (weights) and c (nodes of the next stage).
+    static const double b1[1] = {1.0};
+    static const double b2[2] = {0.5, 0.5}, c2[2] = {1.0, 0.0};
+    static const double b4[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, c4[4] = {0.5, 0.5, 1.0, 0.0};
+    const double *b, *c;
+    static const double c1[1] = {0.0};
+    if (rk_stages == 1) {
+        b = b1;
+        c = c1;
+    } else if (rk_stages == 2) {
+        b = b2;
+        c = c2;
+    } else if (rk_stages == 4) {
+        b = b4;
+        c = c4;
+    } else {
+        return fail(WKE_ERR_INVALID, "rk_stages must be 1, 2 or 4");
+    }
+    const HostPlan &hp = plan->hp;
+    cudaStream_t s = plan->stream;
+    const bool f32 = hp.precision == WKE_FP32;
+    for (int st = 0; st < rk_stages; ++st) {
+        const void *y = st == 0 ? f : plan->rk_y;
+        int rc = collision(plan, y, plan->rk_k, nullptr, s);
+        if (rc) return rc;
+        const bool last = st == rk_stages - 1;
+        void *ynext = last ? nullptr : plan->rk_y;
+        int e = f32 ? rk_stage_T<float>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s)
+                    : rk_stage_T<double>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s);
+        if (e) return cuda_fail((cudaError_t)e, "Runge-Kutta stage");
+    }
+    int e = f32 ? rk_final_T<float>(hp, f, plan->rk_acc, dt, s) : rk_final_T<double>(hp, f, plan->rk_acc, dt, s);
+    if (e) return cuda_fail((cudaError_t)e, "Runge-Kutta update");
+    return WKE_OK;
+}
+
+int wke_moments(wke_plan *plan, const void *g, double *out, void *stream) {
+    if (!plan || !g || !out) return fail(WKE_ERR_INVALID, "plan, g and out must be non-NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int e = plan->hp.precision == WKE_FP32 ? moments_T<float>(plan->hp, g, plan->mom_partials, out, s)
+                                           : moments_T<double>(plan->hp, g, plan->mom_partials, out, s);
+    if (e) return cuda_fail((cudaError_t)e, "moments");
+    return WKE_OK;
+}
+
+int wke_plan_profile(wke_plan *plan, int enable) {
+    if (!plan) return fail(WKE_ERR_INVALID, "plan is NULL");
+    plan->profiling = enable != 0;
+    plan->ev_used = 0;
+    plan->ev_class.clear();
+    return WKE_OK;
+}
+
+int wke_plan_profile_read(wke_plan *plan, double *out) {
+    if (!plan || !out) return fail(WKE_ERR_INVALID, "plan and out must be non-NULL");
+    for (int k = 0; k < 2 * WKE_PROF_CLASSES; ++k) out[k] = 0.0;
+    for (size_t i = 0; i < plan->ev_class.size(); ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, plan->ev_pool[2 * i], plan->ev_pool[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "reading kernel timings (is the stream idle?)");
+        out[2 * plan->ev_class[i]] += ms;
+        out[2 * plan->ev_class[i] + 1] += 1.0;
+    }
+    plan->ev_used = 0;
+    plan->ev_class.clear();
+    return WKE_OK;
+}
+
+const char *wke_last_error_string(void) { return wke::last_error(); }
+
+const char *wke_version(void) { return "wke-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

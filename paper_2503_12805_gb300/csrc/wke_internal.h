@@ -1,0 +1,93 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "wke.h"
+
+namespace wke {
+
+// Thread-local error message for wke_last_error_string().
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+// ---------------------------------------------------------------- host plan
+// Quadrature nodes and the field / product layout of one plan, all in double
+// precision on the host (Sec. 3.3, Eq. (3.8)).
+struct HostPlan {
+    int d = 0, N = 0, M = 0;
+    double L = 0, R = 0;
+    int n_r = 0, n_s = 0, n_sig = 0;
+    int precision = WKE_FP64, nyquist = WKE_NYQ_KEEP, dispersion = WKE_OMEGA_HALF_K2;
+
+    std::vector<double> r, w_r;          // radial nodes / weights on [0, R]
+    std::vector<double> qhat, w_s;       // n_s * d directions, weights
+    std::vector<double> sig, w_sig;      // n_sig * d collision angles, weights
+
+    // Per node p = (p1, p2, p3) in lexicographic order.
+    std::vector<double> W;               // w_r |q|^{2d-3} w_s w_sig
+    std::vector<double> q, a, b;         // shift vectors, M * d each
+
+    // Field layout.  Group g = p1 * n_s + p2 owns fields_per_group shifted
+    // fields f_N(k - x): local field 0 is C (x = q); with antipodal pairing
+    // local field 1 + p3 is f_N(k - a_{p3}) (which is also f_N(k - b) of the
+    // antipodal node), otherwise 1 + 2 p3 is A_{p3} and 2 + 2 p3 is B_{p3}.
+    bool paired = false;
+    std::vector<int> anti;               // sigma index of -sigma (paired only)
+    int fields_per_group = 0, products_per_group = 0, n_groups = 0;
+    std::vector<double> field_shift;     // n_groups * fields_per_group * d
+    std::vector<int> prod_fa, prod_fb;   // products_per_group local field ids
+    std::vector<double> prod_W;          // n_groups * products_per_group weights
+
+    // Chunking of groups through the intermediate buffer.
+    int groups_per_chunk = 0, n_chunks = 0;
+    size_t chunk_bytes = 0;
+
+    double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)
+};
+
+// Validate arguments and fill `hp` (no device work).  Returns WKE_OK or an
+// error code with the message set.
+int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, HostPlan &hp);
+
+// exp(-i pi j x / L) for the signed mode j stored at DFT position `pos`.
+void phase_row(int N, double L, double x, double *out_re_im /* 2N */);
+
+// Device bytes of every buffer a plan with this layout allocates.
+size_t plan_device_bytes(const HostPlan &hp);
+
+// Arithmetic and intermediate-traffic model of one collision (for info).
+double plan_flops(const HostPlan &hp);
+double plan_l2_bytes(const HostPlan &hp);
+
+// ---------------------------------------------------------------- kernels
+// Launch wrappers (wke_kernels_*.cu).  All are asynchronous on `stream`;
+// they return cudaGetLastError() cast to int.
+struct DevicePtrs {
+    // Set by the API layer; element types depend on the precision.
+    const void *f;            // input grid (T)
+    void *ghat;               // N^d complex T: coefficients of f (DFT order)
+    void *fwd_tmp;            // N^d complex double: forward-transform scratch
+    void *H;                  // chunk intermediate fields, complex T
+    double *Qacc;             // groups_per_chunk * N^d partial sums (real)
+    double *Qacc_im;          // groups_per_chunk * N^d partial sums (imag) or null
+    const void *phase;        // n_fields * d * N complex T phase tables
+    const void *tw;           // N complex T twiddles exp(+2 pi i k / N)
+    const double *tw64;       // N complex double twiddles
+    const int *prod_local;    // products_per_group * 2 ints (fa, fb)
+    const double *prod_W;     // n_groups * products_per_group
+};
+
+int launch_forward(const HostPlan &hp, const DevicePtrs &p, void *stream);
+int launch_pass1(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);
+int launch_pass2(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);
+int launch_finalize(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, void *stream);
+int launch_moments(const HostPlan &hp, const void *g, double *partials, double *out, void *stream);
+int moments_partials_count(const HostPlan &hp);
+int launch_rk_stage(const HostPlan &hp, const void *f, const void *k, double *kacc, void *ystage,
+                    double b_s, double c_next_dt, int first, void *stream);
+int launch_rk_final(const HostPlan &hp, void *f, const double *kacc, double dt, void *stream);
+
+}  // namespace wke

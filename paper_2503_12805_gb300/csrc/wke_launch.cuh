@@ -1,0 +1,191 @@
+// Launch wrappers for one real type T; included by the per-precision
+// translation units, which instantiate them explicitly.
+#pragma once
+
+#include <algorithm>
+
+#include "wke_kernels.cuh"
+
+namespace wke {
+
+template <typename K> static int set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return 0;
+}
+
+static inline size_t nd_of(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
+static inline int cols_of(const HostPlan &hp) { return hp.d == 2 ? hp.N : hp.N * hp.N; }
+
+// Warps of a line kernel that walks `lines` independent lines.
+template <typename T, int N> static int line_warps(int lines) {
+    return std::max(1, std::min(KCfg<T>::WARPS, lines / LineCfg<T, N>::LPW));
+}
+
+// ------------------------------------------------------------------ forward
+template <typename T, int N> static int forward_n(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
+    typedef LineCfg<double, N> Cfg;
+    const int P = cols_of(hp);
+    double2 *tmp = static_cast<double2 *>(p.fwd_tmp);
+    const double2 *tw = reinterpret_cast<const double2 *>(p.tw64);
+    int rc = 0;
+    if (hp.d == 3) {
+        if constexpr (N <= 64) {
+            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(double2);
+            if ((rc = set_smem(k_fwd_planes_3d<T, N>, smem))) return rc;
+            k_fwd_planes_3d<T, N><<<N, N * Cfg::TPL, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
+        } else {
+            return (int)cudaErrorInvalidValue;
+        }
+    } else {
+        const int warps = line_warps<double, N>(N);
+        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
+        if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
+        k_fwd_rows_2d<T, N><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
+    }
+    const int warps = line_warps<double, N>(P);
+    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
+    if ((rc = set_smem(k_fwd_cols<T, N>, smem))) return rc;
+    const double inv_nd = 1.0 / (double)nd_of(hp);
+    k_fwd_cols<T, N><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(
+        tmp, static_cast<cx<T> *>(p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO);
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pass 1
+template <typename T, int N>
+static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+    typedef LineCfg<T, N> Cfg;
+    const int nfields = ng * hp.fields_per_group;
+    const int field0 = g0 * hp.fields_per_group;
+    const cx<T> *ghat = static_cast<const cx<T> *>(p.ghat);
+    const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
+    cx<T> *H = static_cast<cx<T> *>(p.H);
+    const cx<T> *tw = static_cast<const cx<T> *>(p.tw);
+    int rc = 0;
+    if (hp.d == 3) {
+        if constexpr (N <= 64) {
+            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
+            if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
+            // enough blocks to fill the GPU several times over
+            const int fpb = std::max(1, std::min(nfields, nfields * N / 1200));
+            dim3 grid(N, (nfields + fpb - 1) / fpb);
+            k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, field0, nfields, fpb);
+        } else {
+            return (int)cudaErrorInvalidValue;
+        }
+    } else {
+        const int warps = line_warps<T, N>(N);
+        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
+        if ((rc = set_smem(k_pass1_2d<T, N>, smem))) return rc;
+        dim3 grid(N / (warps * Cfg::LPW), nfields);
+        k_pass1_2d<T, N><<<grid, warps * 32, smem, s>>>(ghat, ph, H, tw, field0);
+    }
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pass 2
+template <typename T, int N, bool IM>
+static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+    typedef LineCfg<T, N> Cfg;
+    const int P = cols_of(hp);
+    const int warps = line_warps<T, N>(P);
+    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
+    int rc = 0;
+    if ((rc = set_smem(k_pass2<T, N, IM>, smem))) return rc;
+    dim3 grid(P / (warps * Cfg::LPW), ng);
+    k_pass2<T, N, IM><<<grid, warps * 32, smem, s>>>(
+        static_cast<const cx<T> *>(p.H), static_cast<const T *>(p.f), p.Qacc, p.Qacc_im, p.prod_local, p.prod_W,
+        static_cast<const cx<T> *>(p.tw), P, hp.fields_per_group, hp.products_per_group, g0);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int N>
+static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+    return im ? pass2_nim<T, N, true>(hp, p, g0, ng, s) : pass2_nim<T, N, false>(hp, p, g0, ng, s);
+}
+
+// ------------------------------------------------------------------ dispatch on N
+template <typename T> int forward_T(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return forward_n<T, 16>(hp, p, s);
+        case 32: return forward_n<T, 32>(hp, p, s);
+        case 64: return forward_n<T, 64>(hp, p, s);
+        case 128: return forward_n<T, 128>(hp, p, s);
+        case 256: return forward_n<T, 256>(hp, p, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return pass1_n<T, 16>(hp, p, g0, ng, s);
+        case 32: return pass1_n<T, 32>(hp, p, g0, ng, s);
+        case 64: return pass1_n<T, 64>(hp, p, g0, ng, s);
+        case 128: return pass1_n<T, 128>(hp, p, g0, ng, s);
+        case 256: return pass1_n<T, 256>(hp, p, g0, ng, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T>
+int pass2_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return pass2_n<T, 16>(hp, p, g0, ng, im, s);
+        case 32: return pass2_n<T, 32>(hp, p, g0, ng, im, s);
+        case 64: return pass2_n<T, 64>(hp, p, g0, ng, im, s);
+        case 128: return pass2_n<T, 128>(hp, p, g0, ng, im, s);
+        case 256: return pass2_n<T, 256>(hp, p, g0, ng, im, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T>
+int finalize_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cudaStream_t s) {
+    const size_t ND = nd_of(hp);
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
+    k_finalize<T><<<blocks, threads, 0, s>>>(p.Qacc, Qim ? p.Qacc_im : nullptr, hp.groups_per_chunk, ND, hp.scale,
+                                             static_cast<T *>(Q), static_cast<T *>(Qim));
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int moments_T(const HostPlan &hp, const void *g, double *partials, double *out, cudaStream_t s) {
+    k_moments<T><<<kMomentBlocks, kMomentThreads, 0, s>>>(static_cast<const T *>(g), hp.d, hp.N, hp.L, partials);
+    const double h = 2.0 * hp.L / hp.N;
+    const double hd = hp.d == 2 ? h * h : h * h * h;
+    k_moments_reduce<<<1, 32, 0, s>>>(partials, kMomentBlocks, hp.d + 2, hd, out);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int rk_stage_T(const HostPlan &hp, const void *f, const void *k, double *kacc, void *ystage, double b_s,
+               double c_next_dt, int first, cudaStream_t s) {
+    const size_t ND = nd_of(hp);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    k_rk_stage<T><<<blocks, 256, 0, s>>>(static_cast<const T *>(f), static_cast<const T *>(k), kacc,
+                                          static_cast<T *>(ystage), b_s, c_next_dt, first, ND);
+    return (int)cudaGetLastError();
+}
+
+template <typename T> int rk_final_T(const HostPlan &hp, void *f, const double *kacc, double dt, cudaStream_t s) {
+    const size_t ND = nd_of(hp);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    k_rk_final<T><<<blocks, 256, 0, s>>>(static_cast<T *>(f), kacc, dt, ND);
+    return (int)cudaGetLastError();
+}
+
+#define WKE_INSTANTIATE(T)                                                                                   \
+    template int forward_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                         \
+    template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);                 \
+    template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);           \
+    template int finalize_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);        \
+    template int moments_T<T>(const HostPlan &, const void *, double *, double *, cudaStream_t);           \
+    template int rk_stage_T<T>(const HostPlan &, const void *, const void *, double *, void *, double,     \
+                               double, int, cudaStream_t);                                                  \
+    template int rk_final_T<T>(const HostPlan &, void *, const double *, double, cudaStream_t);
+
+}  // namespace wke

@@ -1,0 +1,388 @@
+// Host side of a plan: quadrature nodes, shift vectors, field layout and
+// phase tables, all in double precision (Sec. 3.3, Eq. (3.8)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wke_internal.h"
+
+namespace wke {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+static const double kPi = 3.14159265358979323846264338327950288;
+
+// Gauss-Legendre nodes and weights on [-1, 1], ascending, by Newton's method
+// on the three-term recurrence of the Legendre polynomials.
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = z;
+                p0 = 1.0;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                // one more evaluation of the derivative at the converged node
+                double q0 = 1.0, q1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double q2 = ((2.0 * k - 1.0) * z * q1 - (k - 1.0) * q0) / k;
+                    q0 = q1;
+                    q1 = q2;
+                }
+                if (n == 1) {
+                    q1 = z;
+                    q0 = 1.0;
+                }
+                dp = n * (z * q1 - q0) / (z * z - 1.0);
+                break;
+            }
+        }
+        double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = -z;           // ascending order: negative roots first
+        x[n - 1 - i] = z;
+        w[i] = wi;
+        w[n - 1 - i] = wi;
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// Sphere rules: directions (n * d) and weights (n).
+static int sphere_rule(int d, int n, int rule, int param, const double *user,
+                       std::vector<double> &dir, std::vector<double> &w) {
+    dir.clear();
+    w.clear();
+    if (n < 1) return fail(WKE_ERR_INVALID, "sphere rule needs at least one point");
+    if (rule == WKE_SPHERE_USER) {
+        if (!user) return fail(WKE_ERR_INVALID, "WKE_SPHERE_USER needs a direction table");
+        for (int i = 0; i < n; ++i) {
+            double nn = 0.0;
+            for (int a = 0; a < d; ++a) nn += user[i * (d + 1) + a] * user[i * (d + 1) + a];
+            nn = std::sqrt(nn);
+            if (!(nn > 0.0) || !std::isfinite(nn))
+                return fail(WKE_ERR_INVALID, "user sphere rule has a zero or non-finite direction");
+            for (int a = 0; a < d; ++a) dir.push_back(user[i * (d + 1) + a] / nn);
+            w.push_back(user[i * (d + 1) + d]);
+        }
+        return WKE_OK;
+    }
+    if (d == 2) {
+        if (rule != WKE_SPHERE_MIDPOINT_2D)
+            return fail(WKE_ERR_INVALID, "2D supports the mid-point rule or a user rule");
+        for (int p = 0; p < n; ++p) {
+            double th = (p + 0.5) * 2.0 * kPi / n;
+            dir.push_back(std::cos(th));
+            dir.push_back(std::sin(th));
+            w.push_back(2.0 * kPi / n);
+        }
+        return WKE_OK;
+    }
+    if (rule == WKE_SPHERE_PLATONIC_3D) {
+        const double g = 0.5 * (1.0 + std::sqrt(5.0));   // golden ratio
+        std::vector<double> v;
+        auto push = [&](double x, double y, double z) {
+            v.push_back(x);
+            v.push_back(y);
+            v.push_back(z);
+        };
+        auto cyc = [&](double x, double y, double z) {
+            push(x, y, z);
+            push(z, x, y);
+            push(y, z, x);
+        };
+        const double s2[2] = {1.0, -1.0};
+        if (n == 6) {
+            for (double s : s2) push(s, 0, 0);
+            for (double s : s2) push(0, s, 0);
+            for (double s : s2) push(0, 0, s);
+        } else if (n == 8) {
+            for (double sx : s2)
+                for (double sy : s2)
+                    for (double sz : s2) push(sx, sy, sz);
+        } else if (n == 12) {
+            for (double sy : s2)
+                for (double sz : s2) cyc(0.0, sy, sz * g);
+        } else if (n == 20) {
+            for (double sx : s2)
+                for (double sy : s2)
+                    for (double sz : s2) push(sx, sy, sz);
+            for (double sy : s2)
+                for (double sz : s2) cyc(0.0, sy / g, sz * g);
+        } else {
+            return fail(WKE_ERR_INVALID, "Platonic designs have 6, 8, 12 or 20 points");
+        }
+        for (int i = 0; i < n; ++i) {
+            double nn = std::sqrt(v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] +
+                                  v[3 * i + 2] * v[3 * i + 2]);
+            for (int a = 0; a < 3; ++a) dir.push_back(v[3 * i + a] / nn);
+            w.push_back(4.0 * kPi / n);
+        }
+        return WKE_OK;
+    }
+    if (rule == WKE_SPHERE_PRODUCT_3D) {
+        int nt = param;
+        if (nt < 1 || n % nt != 0)
+            return fail(WKE_ERR_INVALID, "product rule: n must be a multiple of n_theta");
+        int np = n / nt;
+        std::vector<double> ct, wt;
+        gauss_legendre(nt, ct, wt);
+        for (int i = 0; i < nt; ++i) {
+            double st = std::sqrt(std::max(0.0, 1.0 - ct[i] * ct[i]));
+            for (int k = 0; k < np; ++k) {
+                double ph = (k + 0.5) * 2.0 * kPi / np;
+                dir.push_back(st * std::cos(ph));
+                dir.push_back(st * std::sin(ph));
+                dir.push_back(ct[i]);
+                w.push_back(wt[i] * 2.0 * kPi / np);
+            }
+        }
+        return WKE_OK;
+    }
+    return fail(WKE_ERR_INVALID, "unknown sphere rule");
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, HostPlan &hp) {
+    if (!quad) return fail(WKE_ERR_INVALID, "quadrature descriptor is NULL");
+    if (d != 2 && d != 3) return fail(WKE_ERR_INVALID, "d must be 2 or 3");
+    if (!(L > 0.0) || !std::isfinite(L)) return fail(WKE_ERR_INVALID, "L must be positive");
+    if (N < 2 || N % 2) return fail(WKE_ERR_INVALID, "N must be even and >= 2");
+    if (quad->n_r < 1 || quad->n_s < 1 || quad->n_sig < 1)
+        return fail(WKE_ERR_INVALID, "n_r, n_s and n_sig must be >= 1");
+    if ((long long)quad->n_r * quad->n_s * quad->n_sig != (long long)M)
+        return fail(WKE_ERR_INVALID, "M must equal n_r * n_s * n_sig");
+    if (quad->precision != WKE_FP64 && quad->precision != WKE_FP32)
+        return fail(WKE_ERR_INVALID, "precision must be WKE_FP64 or WKE_FP32");
+    if (quad->nyquist != WKE_NYQ_KEEP && quad->nyquist != WKE_NYQ_ZERO)
+        return fail(WKE_ERR_INVALID, "nyquist must be WKE_NYQ_KEEP or WKE_NYQ_ZERO");
+    if (quad->dispersion != WKE_OMEGA_HALF_K2 && quad->dispersion != WKE_OMEGA_K2)
+        return fail(WKE_ERR_INVALID, "unknown dispersion");
+    if (!(quad->R >= 0.0) || !std::isfinite(quad->R)) return fail(WKE_ERR_INVALID, "R must be >= 0");
+    if (!is_pow2(N) || N < 16 || (d == 2 && N > 256) || (d == 3 && N > 64))
+        return fail(WKE_ERR_UNSUPPORTED,
+                    "kernels are built for N a power of two, 16..256 (2D) or 16..64 (3D)");
+
+    hp = HostPlan();
+    hp.d = d;
+    hp.N = N;
+    hp.M = M;
+    hp.L = L;
+    hp.R = quad->R > 0.0 ? quad->R : 4.0 * L / (3.0 + std::sqrt(2.0));
+    hp.n_r = quad->n_r;
+    hp.n_s = quad->n_s;
+    hp.n_sig = quad->n_sig;
+    hp.precision = quad->precision;
+    hp.nyquist = quad->nyquist;
+    hp.dispersion = quad->dispersion;
+
+    // Radial rule: Gauss-Legendre mapped to [0, R].
+    std::vector<double> x, wx;
+    gauss_legendre(hp.n_r, x, wx);
+    for (int i = 0; i < hp.n_r; ++i) {
+        hp.r.push_back(0.5 * hp.R * (x[i] + 1.0));
+        hp.w_r.push_back(0.5 * hp.R * wx[i]);
+    }
+    int rule_s = quad->sphere_rule < 0 ? (d == 2 ? WKE_SPHERE_MIDPOINT_2D : WKE_SPHERE_PLATONIC_3D)
+                                       : quad->sphere_rule;
+    int rule_g = quad->sphere_rule_sig < 0 ? rule_s : quad->sphere_rule_sig;
+    int param_g = quad->sphere_rule_sig < 0 ? quad->sphere_param : quad->sphere_param_sig;
+    int rc = sphere_rule(d, hp.n_s, rule_s, quad->sphere_param, quad->user_s, hp.qhat, hp.w_s);
+    if (rc) return rc;
+    rc = sphere_rule(d, hp.n_sig, rule_g, param_g,
+                     quad->sphere_rule_sig < 0 && rule_g == WKE_SPHERE_USER ? quad->user_s
+                                                                           : quad->user_sig,
+                     hp.sig, hp.w_sig);
+    if (rc) return rc;
+
+    // Antipodal pairing of the sigma rule: sigma_{p'} = -sigma_p with equal
+    // weights makes f_N(k - b_p) identical to f_N(k - a_{p'}) and the node
+    // products of p and p' identical.
+    hp.paired = false;
+    if (quad->pair_antipodal && hp.n_sig % 2 == 0) {
+        hp.anti.assign(hp.n_sig, -1);
+        bool ok = true;
+        for (int i = 0; i < hp.n_sig && ok; ++i) {
+            int found = -1;
+            for (int k = 0; k < hp.n_sig; ++k) {
+                if (k == i) continue;
+                double dev = 0.0;
+                for (int a = 0; a < d; ++a) dev = std::max(dev, std::fabs(hp.sig[k * d + a] + hp.sig[i * d + a]));
+                if (dev < 1e-13 && std::fabs(hp.w_sig[k] - hp.w_sig[i]) <= 1e-14 * std::fabs(hp.w_sig[i])) {
+                    found = k;
+                    break;
+                }
+            }
+            if (found < 0) ok = false;
+            hp.anti[i] = found;
+        }
+        if (ok) {
+            hp.paired = true;
+            // make the pairs exactly antipodal so the shared fields coincide
+            for (int i = 0; i < hp.n_sig; ++i)
+                if (hp.anti[i] > i)
+                    for (int a = 0; a < d; ++a) hp.sig[hp.anti[i] * d + a] = -hp.sig[i * d + a];
+        } else {
+            hp.anti.clear();
+        }
+    }
+
+    // Nodes in (p1, p2, p3) order.
+    hp.W.resize(M);
+    hp.q.resize((size_t)M * d);
+    hp.a.resize((size_t)M * d);
+    hp.b.resize((size_t)M * d);
+    int p = 0;
+    for (int p1 = 0; p1 < hp.n_r; ++p1) {
+        double r = hp.r[p1];
+        double rw = hp.w_r[p1] * std::pow(r, 2 * d - 3);
+        for (int p2 = 0; p2 < hp.n_s; ++p2) {
+            for (int p3 = 0; p3 < hp.n_sig; ++p3, ++p) {
+                hp.W[p] = rw * hp.w_s[p2] * hp.w_sig[p3];
+                for (int a = 0; a < d; ++a) {
+                    double qa = r * hp.qhat[p2 * d + a];
+                    double sa = r * hp.sig[p3 * d + a];
+                    hp.q[(size_t)p * d + a] = qa;
+                    hp.a[(size_t)p * d + a] = 0.5 * (qa - sa);
+                    hp.b[(size_t)p * d + a] = 0.5 * (qa + sa);
+                }
+            }
+        }
+    }
+
+    // Field and product layout per group.
+    hp.n_groups = hp.n_r * hp.n_s;
+    if (hp.paired) {
+        hp.fields_per_group = 1 + hp.n_sig;
+        hp.products_per_group = hp.n_sig / 2;
+        for (int i = 0; i < hp.n_sig; ++i)
+            if (hp.anti[i] > i) {
+                hp.prod_fa.push_back(1 + i);
+                hp.prod_fb.push_back(1 + hp.anti[i]);
+            }
+    } else {
+        hp.fields_per_group = 1 + 2 * hp.n_sig;
+        hp.products_per_group = hp.n_sig;
+        for (int i = 0; i < hp.n_sig; ++i) {
+            hp.prod_fa.push_back(1 + 2 * i);
+            hp.prod_fb.push_back(2 + 2 * i);
+        }
+    }
+    hp.field_shift.assign((size_t)hp.n_groups * hp.fields_per_group * d, 0.0);
+    hp.prod_W.assign((size_t)hp.n_groups * hp.products_per_group, 0.0);
+    for (int g = 0; g < hp.n_groups; ++g) {
+        int node0 = g * hp.n_sig;
+        double *fs = &hp.field_shift[(size_t)g * hp.fields_per_group * d];
+        for (int a = 0; a < d; ++a) fs[a] = hp.q[(size_t)node0 * d + a];
+        for (int i = 0; i < hp.n_sig; ++i) {
+            int node = node0 + i;
+            if (hp.paired) {
+                for (int a = 0; a < d; ++a) fs[(1 + i) * d + a] = hp.a[(size_t)node * d + a];
+            } else {
+                for (int a = 0; a < d; ++a) {
+                    fs[(1 + 2 * i) * d + a] = hp.a[(size_t)node * d + a];
+                    fs[(2 + 2 * i) * d + a] = hp.b[(size_t)node * d + a];
+                }
+            }
+        }
+        if (hp.paired) {
+            int k = 0;
+            for (int i = 0; i < hp.n_sig; ++i)
+                if (hp.anti[i] > i)
+                    hp.prod_W[(size_t)g * hp.products_per_group + k++] = hp.W[node0 + i] + hp.W[node0 + hp.anti[i]];
+        } else {
+            for (int i = 0; i < hp.n_sig; ++i) hp.prod_W[(size_t)g * hp.products_per_group + i] = hp.W[node0 + i];
+        }
+    }
+
+    // Chunks of groups whose intermediate fields fit the byte budget.
+    size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
+    size_t nd = 1;
+    for (int a = 0; a < d; ++a) nd *= (size_t)N;
+    size_t per_group = (size_t)hp.fields_per_group * nd * cxb;
+    hp.chunk_bytes = quad->chunk_bytes ? quad->chunk_bytes : (size_t)48 << 20;
+    hp.groups_per_chunk = (int)std::max<size_t>(1, hp.chunk_bytes / per_group);
+    hp.groups_per_chunk = std::min(hp.groups_per_chunk, hp.n_groups);
+    hp.n_chunks = (hp.n_groups + hp.groups_per_chunk - 1) / hp.groups_per_chunk;
+
+    hp.scale = std::ldexp(1.0, 1 - d) * (hp.dispersion == WKE_OMEGA_K2 ? 0.5 : 1.0);
+    return WKE_OK;
+}
+
+void phase_row(int N, double L, double x, double *out) {
+    for (int pos = 0; pos < N; ++pos) {
+        int j = pos < N / 2 ? pos : pos - N;      // signed mode, -N/2 at pos N/2
+        double th = -kPi * (double)j * x / L;
+        out[2 * pos] = std::cos(th);
+        out[2 * pos + 1] = std::sin(th);
+    }
+}
+
+static size_t grid_size(const HostPlan &hp) {
+    size_t nd = 1;
+    for (int a = 0; a < hp.d; ++a) nd *= (size_t)hp.N;
+    return nd;
+}
+
+size_t plan_device_bytes(const HostPlan &hp) {
+    size_t nd = grid_size(hp);
+    size_t tb = hp.precision == WKE_FP64 ? 8 : 4;
+    size_t cxb = 2 * tb;
+    size_t n_fields = (size_t)hp.n_groups * hp.fields_per_group;
+    size_t bytes = 0;
+    bytes += nd * cxb;                                                  // ghat
+    bytes += std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16);  // H
+    bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
+    bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
+    bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
+    bytes += hp.products_per_group * 2 * sizeof(int);
+    bytes += (size_t)hp.n_groups * hp.products_per_group * 8;
+    bytes += 2 * nd * tb;                                               // host-call staging
+    bytes += 2 * nd * tb + nd * 8;                                      // RK stage, k, k-sum
+    bytes += (size_t)moments_partials_count(hp) * (hp.d + 2) * 8 + (hp.d + 2) * 8;
+    return bytes;
+}
+
+double plan_flops(const HostPlan &hp) {
+    double nd = (double)grid_size(hp);
+    double lg = std::log2(nd);
+    double n_fields = (double)hp.n_groups * hp.fields_per_group;
+    double n_prod = (double)hp.n_groups * hp.products_per_group;
+    double fwd = 5.0 * nd * lg;
+    double inv = n_fields * 5.0 * nd * lg;
+    double phases = n_fields * nd * 12.0;      // two complex products per point
+    double prods = n_prod * nd * 30.0;         // cubic product, weight, accumulate
+    return fwd + inv + phases + prods;
+}
+
+double plan_l2_bytes(const HostPlan &hp) {
+    double nd = (double)grid_size(hp);
+    double cxb = hp.precision == WKE_FP64 ? 16.0 : 8.0;
+    double n_fields = (double)hp.n_groups * hp.fields_per_group;
+    return n_fields * nd * cxb * 2.0;          // each intermediate written once, read once
+}
+
+}  // namespace wke

@@ -1,0 +1,306 @@
+"""Python binding of the C-ABI library ``libwke.so`` (ctypes).
+
+Argument marshalling only: every step of the collision operator runs in the
+library's CUDA kernels.  The functions keep the C names; ``Plan`` is a small
+convenience wrapper that passes torch CUDA tensors' pointers and streams.
+Importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwke.so")
+
+WKE_OK = 0
+WKE_ERR_INVALID = -1
+WKE_ERR_OOM = -2
+WKE_ERR_CUDA = -3
+WKE_ERR_UNSUPPORTED = -4
+
+WKE_SPHERE_DEFAULT = -1
+WKE_SPHERE_MIDPOINT_2D = 0
+WKE_SPHERE_PLATONIC_3D = 1
+WKE_SPHERE_PRODUCT_3D = 2
+WKE_SPHERE_USER = 3
+
+WKE_FP64 = 0
+WKE_FP32 = 1
+WKE_NYQ_KEEP = 0
+WKE_NYQ_ZERO = 1
+WKE_OMEGA_HALF_K2 = 0
+WKE_OMEGA_K2 = 1
+
+C_DOUBLE_P = ctypes.POINTER(ctypes.c_double)
+
+
+class WkeQuadrature(ctypes.Structure):
+    _fields_ = [
+        ("n_r", ctypes.c_int), ("n_s", ctypes.c_int), ("n_sig", ctypes.c_int),
+        ("sphere_rule", ctypes.c_int), ("sphere_rule_sig", ctypes.c_int),
+        ("sphere_param", ctypes.c_int), ("sphere_param_sig", ctypes.c_int),
+        ("user_s", C_DOUBLE_P), ("user_sig", C_DOUBLE_P),
+        ("R", ctypes.c_double), ("precision", ctypes.c_int), ("nyquist", ctypes.c_int),
+        ("dispersion", ctypes.c_int), ("pair_antipodal", ctypes.c_int),
+        ("chunk_bytes", ctypes.c_size_t),
+    ]
+
+
+class WkePlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int), ("precision", ctypes.c_int),
+        ("n_groups", ctypes.c_int), ("fields_per_group", ctypes.c_int),
+        ("products_per_group", ctypes.c_int), ("groups_per_chunk", ctypes.c_int),
+        ("n_chunks", ctypes.c_int), ("launches_per_collision", ctypes.c_int),
+        ("flops_per_collision", ctypes.c_double), ("l2_bytes_per_collision", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+EXPORTED = [
+    "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
+    "wke_plan_get_info", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
+    "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
+    "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
+]
+PROF_CLASSES = ("forward", "pass1", "pass2", "finalize")
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libwke.so is not built ({path}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    QP = ctypes.POINTER(WkeQuadrature)
+    sig = {
+        "wke_quadrature_default": (i, [QP]),
+        "wke_plan_create": (i, [i, i, d, i, QP, ctypes.POINTER(vp)]),
+        "wke_plan_destroy": (i, [vp]),
+        "wke_plan_footprint_bytes": (i, [i, i, d, i, QP, ctypes.POINTER(sz)]),
+        "wke_plan_get_info": (i, [vp, ctypes.POINTER(WkePlanInfo)]),
+        "wke_plan_node_table": (i, [vp, C_DOUBLE_P]),
+        "wke_collision": (i, [vp, vp, vp, vp]),
+        "wke_collision_ex": (i, [vp, vp, vp, vp, vp]),
+        "wke_collision_host": (i, [vp, vp, vp]),
+        "wke_plan_set_stream": (i, [vp, vp]),
+        "wke_step": (i, [vp, vp, d, i]),
+        "wke_moments": (i, [vp, vp, vp, vp]),
+        "wke_plan_profile": (i, [vp, i]),
+        "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
+        "wke_last_error_string": (ctypes.c_char_p, []),
+        "wke_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class WkeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"wke error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int) -> None:
+    if rc != WKE_OK:
+        raise WkeError(rc, lib().wke_last_error_string().decode())
+
+
+# ------------------------------------------------------------ C-named calls
+
+def wke_quadrature_default() -> WkeQuadrature:
+    q = WkeQuadrature()
+    _check(lib().wke_quadrature_default(ctypes.byref(q)))
+    return q
+
+
+def wke_plan_create(d: int, N: int, L: float, M: int, quad: WkeQuadrature) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(lib().wke_plan_create(d, N, L, M, ctypes.byref(quad), ctypes.byref(out)))
+    return out
+
+
+def wke_plan_destroy(plan) -> None:
+    _check(lib().wke_plan_destroy(plan))
+
+
+def wke_plan_footprint_bytes(d: int, N: int, L: float, M: int, quad: WkeQuadrature) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().wke_plan_footprint_bytes(d, N, L, M, ctypes.byref(quad), ctypes.byref(out)))
+    return out.value
+
+
+def wke_plan_get_info(plan) -> WkePlanInfo:
+    info = WkePlanInfo()
+    _check(lib().wke_plan_get_info(plan, ctypes.byref(info)))
+    return info
+
+
+def wke_collision(plan, f_ptr: int, Q_ptr: int, stream: int = 0) -> None:
+    _check(lib().wke_collision(plan, f_ptr, Q_ptr, stream))
+
+
+def wke_collision_ex(plan, f_ptr: int, Q_ptr: int, Qim_ptr: int | None, stream: int = 0) -> None:
+    _check(lib().wke_collision_ex(plan, f_ptr, Q_ptr, Qim_ptr, stream))
+
+
+def wke_collision_host(plan, f_host_ptr: int, Q_host_ptr: int) -> None:
+    _check(lib().wke_collision_host(plan, f_host_ptr, Q_host_ptr))
+
+
+def wke_plan_set_stream(plan, stream: int) -> None:
+    _check(lib().wke_plan_set_stream(plan, stream))
+
+
+def wke_step(plan, f_ptr: int, dt: float, rk_stages: int) -> None:
+    _check(lib().wke_step(plan, f_ptr, dt, rk_stages))
+
+
+def wke_moments(plan, g_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check(lib().wke_moments(plan, g_ptr, out_ptr, stream))
+
+
+def wke_plan_profile(plan, enable: bool) -> None:
+    _check(lib().wke_plan_profile(plan, int(enable)))
+
+
+def wke_plan_profile_read(plan) -> dict:
+    """{class: (total_ms, launches)} recorded since profiling was enabled."""
+    out = (ctypes.c_double * (2 * len(PROF_CLASSES)))()
+    _check(lib().wke_plan_profile_read(plan, out))
+    return {c: (out[2 * i], int(out[2 * i + 1])) for i, c in enumerate(PROF_CLASSES)}
+
+
+# ------------------------------------------------------------ torch helper
+
+SPHERE_NAMES = {"midpoint": WKE_SPHERE_MIDPOINT_2D, "platonic": WKE_SPHERE_PLATONIC_3D,
+                "cube": WKE_SPHERE_PLATONIC_3D, "octahedron": WKE_SPHERE_PLATONIC_3D,
+                "icosahedron": WKE_SPHERE_PLATONIC_3D, "dodecahedron": WKE_SPHERE_PLATONIC_3D}
+
+
+def _rule(name: str | None):
+    """(rule, param) for a rule name; 'product:nt:nphi' gives the product rule."""
+    if name is None:
+        return WKE_SPHERE_DEFAULT, 0
+    if name.startswith("product:"):
+        return WKE_SPHERE_PRODUCT_3D, int(name.split(":")[1])
+    return SPHERE_NAMES[name], 0
+
+
+class Plan:
+    """A plan on the current CUDA device; tensors are torch CUDA tensors."""
+
+    def __init__(self, d: int, N: int, L: float, n_r: int, n_s: int, n_sig: int,
+                 sphere: str | None = None, sphere_sig: str | None = None, R: float = 0.0,
+                 precision: str = "fp64", nyquist: str = "keep", pair_antipodal: bool = True,
+                 chunk_bytes: int = 0, dispersion: str = "half_k2", user_s=None, user_sig=None):
+        import numpy as np
+        q = wke_quadrature_default()
+        q.n_r, q.n_s, q.n_sig = n_r, n_s, n_sig
+        q.sphere_rule, q.sphere_param = _rule(sphere)
+        if sphere_sig is not None:
+            q.sphere_rule_sig, q.sphere_param_sig = _rule(sphere_sig)
+        self._keep = []
+        if user_s is not None:
+            arr = np.ascontiguousarray(user_s, dtype=np.float64)
+            self._keep.append(arr)
+            q.sphere_rule = WKE_SPHERE_USER
+            q.user_s = arr.ctypes.data_as(C_DOUBLE_P)
+        if user_sig is not None:
+            arr = np.ascontiguousarray(user_sig, dtype=np.float64)
+            self._keep.append(arr)
+            q.sphere_rule_sig = WKE_SPHERE_USER
+            q.user_sig = arr.ctypes.data_as(C_DOUBLE_P)
+        q.R = R
+        q.precision = {"fp64": WKE_FP64, "fp32": WKE_FP32}[precision]
+        q.nyquist = {"keep": WKE_NYQ_KEEP, "zero": WKE_NYQ_ZERO}[nyquist]
+        q.dispersion = {"half_k2": WKE_OMEGA_HALF_K2, "k2": WKE_OMEGA_K2}[dispersion]
+        q.pair_antipodal = int(pair_antipodal)
+        q.chunk_bytes = chunk_bytes
+        self.d, self.N, self.L = d, N, L
+        self.M = n_r * n_s * n_sig
+        self.precision = precision
+        self.handle = wke_plan_create(d, N, L, self.M, q)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def info(self) -> WkePlanInfo:
+        return wke_plan_get_info(self.handle)
+
+    def node_table(self):
+        import numpy as np
+        out = np.zeros((self.M, 1 + 3 * self.d), dtype=np.float64)
+        _check(lib().wke_plan_node_table(self.handle, out.ctypes.data_as(C_DOUBLE_P)))
+        return out
+
+    def _check_grid(self, t):
+        import torch
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()
+                and tuple(t.shape) == (self.N,) * self.d):
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor of shape {(self.N,) * self.d}")
+        return t
+
+    def collision(self, f, Q=None, Qim=None, stream=None):
+        import torch
+        self._check_grid(f)
+        if Q is None:
+            Q = torch.empty_like(f)
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        wke_collision_ex(self.handle, f.data_ptr(), self._check_grid(Q).data_ptr(),
+                         None if Qim is None else self._check_grid(Qim).data_ptr(), s)
+        return Q
+
+    def step(self, f, dt: float, rk_stages: int = 4, stream=None):
+        import torch
+        self._check_grid(f)
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        wke_plan_set_stream(self.handle, s)
+        wke_step(self.handle, f.data_ptr(), dt, rk_stages)
+        return f
+
+    def moments(self, g, stream=None):
+        import torch
+        self._check_grid(g)
+        out = torch.empty(self.d + 2, dtype=torch.float64, device=g.device)
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        wke_moments(self.handle, g.data_ptr(), out.data_ptr(), s)
+        return out
+
+    def collision_host(self, f_host, Q_host):
+        """f_host, Q_host: CPU tensors (pinned for full bandwidth) of the plan dtype."""
+        wke_collision_host(self.handle, f_host.data_ptr(), Q_host.data_ptr())
+        return Q_host
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wke_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every function include/wke.h declares,
+and rejects bad arguments with error codes (no GPU work involved)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def wke():
+    from paper_2503_12805_gb300 import build, wke as w
+    build()
+    w.lib()
+    return w
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(wke_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(wke):
+    names = _declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(wke.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(wke.EXPORTED) <= set(names)
+
+
+def test_version_and_defaults(wke):
+    assert b"sm_103a" in wke.lib().wke_version()
+    q = wke.wke_quadrature_default()
+    assert q.precision == wke.WKE_FP64 and q.pair_antipodal == 1 and q.sphere_rule == -1
+
+
+@pytest.mark.parametrize("d,N,L,M,nr,ns,nsig,code", [
+    (4, 32, 8.0, 8, 2, 2, 2, -1),        # bad dimension
+    (2, 32, -1.0, 8, 2, 2, 2, -1),       # bad L
+    (2, 32, 8.0, 9, 2, 2, 2, -1),        # M != n_r n_s n_sig
+    (2, 33, 8.0, 8, 2, 2, 2, -1),        # odd N
+    (2, 48, 8.0, 8, 2, 2, 2, -4),        # valid N, no kernel built
+    (3, 128, 8.0, 64, 1, 8, 8, -4),      # 3D N=128 not built
+    (3, 32, 8.0, 2 * 7 * 8, 2, 7, 8, -1),  # no Platonic design with 7 points
+])
+def test_invalid_arguments_return_codes(wke, d, N, L, M, nr, ns, nsig, code):
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = nr, ns, nsig
+    size = ctypes.c_size_t()
+    rc = wke.lib().wke_plan_footprint_bytes(d, N, L, M, ctypes.byref(q), ctypes.byref(size))
+    assert rc == code
+    assert wke.lib().wke_last_error_string()
+    out = ctypes.c_void_p(123)
+    assert wke.lib().wke_plan_create(d, N, L, M, ctypes.byref(q), ctypes.byref(out)) == code
+    assert out.value is None
+
+
+def test_null_arguments(wke):
+    lib = wke.lib()
+    assert lib.wke_quadrature_default(None) == wke.WKE_ERR_INVALID
+    assert lib.wke_collision(None, None, None, None) == wke.WKE_ERR_INVALID
+    assert lib.wke_step(None, None, 0.1, 4) == wke.WKE_ERR_INVALID
+    assert lib.wke_plan_destroy(None) == wke.WKE_OK
+
+
+def test_footprint_scales_with_precision_and_chunk(wke):
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = 32, 8, 8
+    b64 = wke.wke_plan_footprint_bytes(3, 64, 8.0, 2048, q)
+    q.precision = wke.WKE_FP32
+    b32 = wke.wke_plan_footprint_bytes(3, 64, 8.0, 2048, q)
+    q.chunk_bytes = 8 << 20
+    b32s = wke.wke_plan_footprint_bytes(3, 64, 8.0, 2048, q)
+    assert b32s < b32 < b64

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (relative max-norm against the oracle's max |Q|): FP64 1e-12,
+FP32 1e-5.  Inputs are the seeded generators of ``wke_inputs``.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import wke_inputs as I
+from oracle import wke_oracle as O
+from tests.gpu_util import gpu_collision, rel_max_err, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _plan(wke, d, N, L, n_r, n_s, n_sig, sphere=None, sphere_sig=None, **kw):
+    return wke.Plan(d, N, L, n_r, n_s, n_sig, sphere=sphere, sphere_sig=sphere_sig, **kw)
+
+
+def _oracle_quad(d, L, n_r, n_s, n_sig, sphere, sphere_sig=None, R=None):
+    return O.make_quadrature(d, n_r, n_s, n_sig, R or O.default_R(L), sphere, sphere_sig)
+
+
+CASES = [
+    # name, d, N, n_r, n_s, n_sig, sphere, sphere_sig, input
+    ("2d_n16_m32 workload", 2, 16, 8, 4, 1, "midpoint", None, lambda: I.WORKLOADS["2d_n16_m32"].initial()),
+    ("2d_n16 Rayleigh-Jeans", 2, 16, 8, 4, 1, "midpoint", None,
+     lambda: I.rayleigh_jeans(2, 16, 8.0, 1.0, [0.0, 0.0], 0.1)),
+    ("2d_n32 paired", 2, 32, 6, 4, 4, "midpoint", None, lambda: I.two_gaussians(32, 8.0, 5)),
+    ("2d_n32 odd sigma rule", 2, 32, 5, 5, 3, "midpoint", None, lambda: I.gaussian_noise(2, 32, 8.0, 9, 0.2)),
+    ("2d_n64", 2, 64, 4, 6, 6, "midpoint", None, lambda: I.two_gaussians(64, 8.0, 6)),
+    ("2d_n256", 2, 256, 3, 4, 4, "midpoint", None, lambda: I.two_gaussians(256, 8.0, 7)),
+    ("3d_n16 cube", 3, 16, 3, 8, 8, "cube", None, lambda: I.gaussian_noise(3, 16, 8.0, 11, 0.1)),
+    ("3d_n16 non-antipodal sigma", 3, 16, 2, 8, 6, "cube", "product:2:3",
+     lambda: I.gaussian_noise(3, 16, 8.0, 12, 0.1)),
+    ("3d_n32 icosahedron/dodecahedron", 3, 32, 2, 12, 20, "icosahedron", "dodecahedron",
+     lambda: I.ring(3, 32, 8.0)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_full_field_parity(case, prec):
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    name, d, N, n_r, n_s, n_sig, sph, sph_sig, gen = case
+    L = 8.0
+    f = gen()
+    ref = O.collision_fast(f, L, _oracle_quad(d, L, n_r, n_s, n_sig, sph, sph_sig), return_complex=True)
+    with _plan(wke, d, N, L, n_r, n_s, n_sig, sph, sph_sig, precision=prec) as plan:
+        Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
+    scale = np.max(np.abs(ref))
+    assert rel_max_err(Q, ref.real, scale) <= TOL[prec], name
+    assert rel_max_err(Qim, ref.imag, scale) <= TOL[prec], name
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload_3d_n32_m1024(prec):
+    """3D N=32, M=1024 (16 radial x 8 x 8 cube directions), Gaussian with 1%
+    seeded noise: full field."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["3d_n32_m1024"]
+    f = w.initial()
+    ref, _ = O.collision_fast(f, w.L, _oracle_quad(3, w.L, w.n_r, w.n_s, w.n_sig, w.sphere))
+    with _plan(wke, 3, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+        Q = gpu_collision(torch, plan, f)
+    assert rel_max_err(Q, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload_2d_n128_m512(prec):
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["2d_n128_m512"]
+    f = w.initial()
+    ref, _ = O.collision_fast(f, w.L, _oracle_quad(2, w.L, w.n_r, w.n_s, w.n_sig, w.sphere))
+    with _plan(wke, 2, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+        Q = gpu_collision(torch, plan, f)
+    assert rel_max_err(Q, ref) <= TOL[prec]
+
+
+def _ring_sample_points(N, L, count, seed):
+    """Grid indices on and near the ring |k| = 3 (where Q is large), plus
+    seeded random points."""
+    k = O.grid_1d(N, L)
+    pts = []
+    u = I.splitmix64_uniform(seed, 4 * count)
+    for i in range(count):
+        th, ph = math.pi * u[4 * i], 2 * math.pi * u[4 * i + 1]
+        rad = 2.5 + 1.0 * u[4 * i + 2]
+        x = rad * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        pts.append(tuple(int(np.argmin(np.abs(k - xa))) for xa in x))
+    pts.append(tuple(int(v) for v in np.floor(u[:3] * N)))
+    return pts
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload_3d_n64_m2048_sampled(prec):
+    """The headline size, in the configuration the benchmark times (default
+    chunking): sampled points against the oracle's direct series evaluation."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["3d_n64_m2048"]
+    f = w.initial()
+    pts = _ring_sample_points(w.N, w.L, 5, 4242)
+    ref = O.collision_at_points(f, w.L, _oracle_quad(3, w.L, w.n_r, w.n_s, w.n_sig, w.sphere), pts)
+    with _plan(wke, 3, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+        Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
+    got = np.array([Q[p] for p in pts])
+    goti = np.array([Qim[p] for p in pts])
+    scale = np.max(np.abs(ref))
+    assert rel_max_err(got, ref.real, scale) <= TOL[prec]
+    assert rel_max_err(goti, ref.imag, scale) <= TOL[prec]
+
+
+def test_3d_n64_full_field_small_quadrature():
+    """N = 64 in 3D over the whole grid (fewer nodes so the oracle stays fast)."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.ring(3, 64, 8.0)
+    ref, _ = O.collision_fast(f, 8.0, _oracle_quad(3, 8.0, 2, 8, 8, "cube"))
+    for prec in ("fp64", "fp32"):
+        with _plan(wke, 3, 64, 8.0, 2, 8, 8, "cube", precision=prec) as plan:
+            Q = gpu_collision(torch, plan, f)
+        assert rel_max_err(Q, ref) <= TOL[prec], prec
+
+
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 16)])
+def test_nyquist_zero_mode(d, N):
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    sph = "midpoint" if d == 2 else "cube"
+    f = I.gaussian_noise(d, N, 8.0, 31, 0.3)
+    quad = _oracle_quad(d, 8.0, 3, 4 if d == 2 else 8, 4 if d == 2 else 8, sph)
+    ref = O.collision_fast(f, 8.0, quad, nyquist="zero", return_complex=True)
+    with _plan(wke, d, N, 8.0, quad.n_r, quad.n_s, quad.n_sig, sph, nyquist="zero") as plan:
+        Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
+    assert rel_max_err(Q, ref.real) <= 1e-12
+    assert np.max(np.abs(Qim)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_pairing_and_chunking_do_not_change_the_sum():
+    """Antipodal pairing (shared fields and products) and the chunk size only
+    reorder the same sum."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.gaussian_noise(3, 32, 8.0, 41, 0.05)
+    res = []
+    for pair, chunk in ((True, 0), (False, 0), (True, 1), (False, 3 << 20)):
+        with _plan(wke, 3, 32, 8.0, 5, 8, 8, "cube", pair_antipodal=pair, chunk_bytes=chunk) as plan:
+            info = plan.info()
+            assert info.fields_per_group == (9 if pair else 17)
+            res.append(gpu_collision(torch, plan, f))
+    for r in res[1:]:
+        assert rel_max_err(r, res[0]) <= 1e-13
+
+
+def test_deterministic_repeat():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.ring(3, 32, 8.0)
+    with _plan(wke, 3, 32, 8.0, 4, 8, 8, "cube", precision="fp32") as plan:
+        a = gpu_collision(torch, plan, f)
+        b = gpu_collision(torch, plan, f)
+    assert np.array_equal(a, b)
+
+
+def test_dispersion_k2_halves_q():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.two_gaussians(32, 8.0, 3)
+    with _plan(wke, 2, 32, 8.0, 4, 4, 4, "midpoint") as p1, \
+            _plan(wke, 2, 32, 8.0, 4, 4, 4, "midpoint", dispersion="k2") as p2:
+        a = gpu_collision(torch, p1, f)
+        b = gpu_collision(torch, p2, f)
+    assert rel_max_err(b, 0.5 * a) <= 1e-15
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_moments_match_oracle(prec):
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    for d, N in ((2, 64), (3, 32)):
+        g = I.two_gaussians(N, 8.0, 2) if d == 2 else I.ring(3, N, 8.0)
+        with _plan(wke, d, N, 8.0, 2, 4 if d == 2 else 8, 4 if d == 2 else 8, precision=prec) as plan:
+            gt = torch.tensor(g, dtype=plan.dtype, device="cuda")
+            m = plan.moments(gt).cpu().numpy()
+        ref = O.moments(gt.double().cpu().numpy(), 8.0)
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(m - ref)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("stages", [1, 2, 4])
+def test_rk_step_matches_oracle(stages):
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    N, L, dt = 32, 8.0, 0.05
+    f0 = I.two_gaussians(N, L, 8)
+    quad = _oracle_quad(2, L, 6, 4, 4, "midpoint")
+    ref = f0.copy()
+    for _ in range(2):
+        ref = O.rk_step(ref, L, quad, dt, stages)
+    with _plan(wke, 2, N, L, 6, 4, 4, "midpoint") as plan:
+        ft = torch.tensor(f0, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            plan.step(ft, dt, stages)
+        torch.cuda.synchronize()
+        got = ft.cpu().numpy()
+    change = np.max(np.abs(ref - f0))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * change
+
+
+def test_host_buffer_call_matches_device_call():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.ring(3, 32, 8.0).astype(np.float32)
+    with _plan(wke, 3, 32, 8.0, 3, 8, 8, "cube", precision="fp32") as plan:
+        dev = gpu_collision(torch, plan, f)
+        fh = torch.tensor(f).pin_memory()
+        qh = torch.empty_like(fh).pin_memory()
+        plan.collision_host(fh, qh)
+    assert np.array_equal(qh.double().numpy(), dev)
