@@ -161,7 +161,8 @@ def run_gpu(args, rank, world, pool, workers):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def make(prec):
-        return wke.Plan(w.d, w.N, w.L, w.n_r, w.n_s, w.n_sig, sphere=w.sphere, precision=prec)
+        return wke.Plan(w.d, w.N, w.L, w.n_r, w.n_s, w.n_sig, sphere=w.sphere, precision=prec,
+                        chunk_bytes=int(args.chunk_mb * (1 << 20)))
 
     def timed(plan, f, Q, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -190,14 +191,22 @@ def run_gpu(args, rank, world, pool, workers):
             torch.distributed.barrier()
         return ms, wall, prof
 
-    # FP32 headline
+    # FP32 headline (no per-kernel events in this loop)
     p32 = make("fp32")
     info = p32.info()
     f32 = torch.tensor(f64, dtype=torch.float32, device=dev)
     Q32 = torch.empty_like(f32)
     with ClockSampler(dev.index) as clk:
-        ms32, wall32, prof = timed(p32, f32, Q32, args.steps, args.warmup, profile=True)
+        ms32, wall32, _ = timed(p32, f32, Q32, args.steps, args.warmup)
     clocks = clk.summary()
+    # per-kernel CUDA-event timings for the roofline, in a second timed loop
+    _, _, prof = timed(p32, f32, Q32, min(args.steps, 20), 1, profile=True)
+    if args.fp32_only:
+        line = {"metric": METRIC, "value": round(1000.0 / (sum(ms32) / len(ms32)), 3), "unit": UNIT,
+                "kernels_ms": prof, "plan": {"groups_per_chunk": info.groups_per_chunk,
+                                              "n_chunks": info.n_chunks}, "clocks": clocks}
+        p32.close()
+        return line
     t_step = sum(ms32) / len(ms32)
     t_max = t_step
     if world > 1:
@@ -321,12 +330,16 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--oracle-nodes", type=int, default=16,
                     help="oracle nodes per host process per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-only", action="store_true",
+                    help="only the FP32 timing and kernel split (profiling runs)")
+    ap.add_argument("--chunk-mb", type=float, default=0.0,
+                    help="intermediate-field budget per chunk in MiB (0: library default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -338,7 +351,7 @@ def main():
         return
     # the oracle's process pool starts before the first GPU call
     pool, workers = (None, 0)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not (args.no_cpu_baseline or args.fp32_only):
         pool, workers = make_pool()
     if world > 1:
         import torch
