@@ -186,12 +186,20 @@ int wke_step(wke_plan *plan, void *f_dev, double dt, int rk_stages);
  * a device pointer to d + 2 doubles.  Asynchronous on `stream`. */
 int wke_moments(wke_plan *plan, const void *g_dev, double *out_dev, void *stream);
 
+/* Evaluations are captured into a CUDA graph per distinct (f, Q, Qim)
+ * pointer set on first use and replayed afterwards (default on; at most 8
+ * graphs per plan).  enable = 0 launches every kernel directly instead.  A
+ * capture runs on the plan's own streams, so the first call with a new
+ * pointer set must not itself be inside a caller's stream capture. */
+int wke_plan_use_graphs(wke_plan *plan, int enable);
+
 /* Kernel timing.  While enabled, every wke_collision records CUDA events
  * around its launches on the call's stream (no host synchronisation).
  * wke_plan_profile_read() must be called after that stream is idle: it adds
  * up the recorded intervals per kernel class into out_host[2 * WKE_PROF_CLASSES]
  * as (total milliseconds, number of launches) pairs, in the order forward,
- * pass 1, pass 2, finalize, and forgets them.  Enabling resets the record. */
+ * pass 1, pass 2, finalize, and forgets them.  Enabling resets the record.
+ * While enabled, evaluations launch directly (no graph replay). */
 #define WKE_PROF_CLASSES 4
 int wke_plan_profile(wke_plan *plan, int enable);
 int wke_plan_profile_read(wke_plan *plan, double *out_host);

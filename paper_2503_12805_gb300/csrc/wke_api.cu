@@ -31,9 +31,25 @@ static int cuda_fail(cudaError_t e, const char *what) {
 
 using namespace wke;
 
+// An instantiated graph of one evaluation for a given (f, Q, Qim).
+struct GraphEntry {
+    const void *f;
+    void *Q;
+    void *Qim;
+    cudaGraphExec_t exec;
+    unsigned long long used;
+};
+
 struct wke_plan {
     HostPlan hp;
     DevicePtrs dp{};
+    void *Hbuf[2] = {nullptr, nullptr};   // double-buffered chunk intermediates
+    // pass 1 of chunk c+1 runs on s1 while pass 2 of chunk c runs on s2
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
+    bool use_graphs = true;
+    std::vector<GraphEntry> graphs;
+    unsigned long long tick = 0;
     std::vector<void *> allocs;
     void *f_stage = nullptr, *Q_stage = nullptr;   // wke_collision_host buffers
     void *rk_y = nullptr, *rk_k = nullptr;
@@ -70,7 +86,18 @@ int dev_alloc(wke_plan *p, void **ptr, size_t bytes) {
     return WKE_OK;
 }
 
+void free_graphs(wke_plan *p) {
+    for (GraphEntry &g : p->graphs) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+}
+
 void free_plan(wke_plan *p) {
+    free_graphs(p);
+    for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_p1[0], p->ev_p1[1], p->ev_p2[0], p->ev_p2[1]})
+        if (e) cudaEventDestroy(e);
+    if (p->s1) cudaStreamDestroy(p->s1);
+    if (p->s2) cudaStreamDestroy(p->s2);
+    p->s1 = p->s2 = nullptr;
     for (void *ptr : p->allocs) cudaFree(ptr);
     p->allocs.clear();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -171,41 +198,109 @@ int clear_accumulators(wke_plan *p, cudaStream_t s) {
     return WKE_OK;
 }
 
-template <typename T> int collision_T(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t s) {
+// Enqueue one evaluation: fork from `origin` to the plan's two streams, the
+// forward transform and pass 1 of each chunk on s1, pass 2 of each chunk on
+// s2 (chunk c uses intermediate buffer c % 2), finalize on s2, join back.
+template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t origin) {
     HostPlan &hp = p->hp;
-    p->dp.f = f;
-    int rc;
-    if (p->dirty && (rc = clear_accumulators(p, s))) return rc;
-    int e;
-    {
-        ProfScope ps(p, s, 0);
-        e = forward_T<T>(hp, p->dp, s);
+    DevicePtrs dp = p->dp;
+    dp.f = f;
+    dp.H = p->Hbuf[0];
+    dp.fwd_tmp = p->Hbuf[0];
+    cudaStream_t s1 = p->s1, s2 = p->s2;
+    int e = (int)cudaEventRecord(p->ev_fork, origin);
+    if (!e) e = (int)cudaStreamWaitEvent(s1, p->ev_fork, 0);
+    if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_fork, 0);
+    if (!e) {
+        ProfScope ps(p, s1, 0);
+        e = forward_T<T>(hp, dp, s1);
     }
     for (int c = 0; c < hp.n_chunks && !e; ++c) {
         const int g0 = c * hp.groups_per_chunk;
         const int ng = std::min(hp.groups_per_chunk, hp.n_groups - g0);
-        {
-            ProfScope ps(p, s, 1);
-            e = pass1_T<T>(hp, p->dp, g0, ng, s);
-        }
+        const int buf = c & 1;
+        dp.H = p->Hbuf[buf];
+        if (c >= 2) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
         if (!e) {
-            ProfScope ps(p, s, 2);
-            e = pass2_T<T>(hp, p->dp, g0, ng, Qim != nullptr, s);
+            ProfScope ps(p, s1, 1);
+            e = pass1_T<T>(hp, dp, g0, ng, s1);
         }
+        if (!e) e = (int)cudaEventRecord(p->ev_p1[buf], s1);
+        if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_p1[buf], 0);
+        if (!e) {
+            ProfScope ps(p, s2, 2);
+            e = pass2_T<T>(hp, dp, g0, ng, Qim != nullptr, s2);
+        }
+        if (!e) e = (int)cudaEventRecord(p->ev_p2[buf], s2);
     }
     if (!e) {
-        ProfScope ps(p, s, 3);
-        e = finalize_T<T>(hp, p->dp, Q, Qim, s);
+        ProfScope ps(p, s2, 3);
+        e = finalize_T<T>(hp, dp, Q, Qim, s2);
+    }
+    if (!e) e = (int)cudaEventRecord(p->ev_join, s2);
+    if (!e) e = (int)cudaStreamWaitEvent(origin, p->ev_join, 0);
+    return e;
+}
+
+int enqueue(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t origin) {
+    return p->hp.precision == WKE_FP32 ? enqueue_T<float>(p, f, Q, Qim, origin)
+                                       : enqueue_T<double>(p, f, Q, Qim, origin);
+}
+
+// The instantiated graph for (f, Q, Qim), captured on first use.  At most 8
+// are kept per plan (least recently used evicted).
+int graph_for(wke_plan *p, const void *f, void *Q, void *Qim, cudaGraphExec_t *out) {
+    for (GraphEntry &g : p->graphs)
+        if (g.f == f && g.Q == Q && g.Qim == Qim) {
+            g.used = ++p->tick;
+            *out = g.exec;
+            return WKE_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(p->s1, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture start");
+    int e = enqueue(p, f, Q, Qim, p->s1);
+    ce = cudaStreamEndCapture(p->s1, &graph);
+    if (e || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return cuda_fail(e ? (cudaError_t)e : ce, "graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiation");
+    if (p->graphs.size() >= 8) {
+        size_t lru = 0;
+        for (size_t i = 1; i < p->graphs.size(); ++i)
+            if (p->graphs[i].used < p->graphs[lru].used) lru = i;
+        cudaGraphExecDestroy(p->graphs[lru].exec);
+        p->graphs.erase(p->graphs.begin() + lru);
+    }
+    p->graphs.push_back({f, Q, Qim, exec, ++p->tick});
+    *out = exec;
+    return WKE_OK;
+}
+
+int collision(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t s) {
+    int rc;
+    if (p->dirty && (rc = clear_accumulators(p, s))) return rc;
+    int e;
+    if (p->use_graphs && !p->profiling) {
+        cudaGraphExec_t exec;
+        if ((rc = graph_for(p, f, Q, Qim, &exec))) {
+            p->dirty = true;
+            return rc;
+        }
+        e = (int)cudaGraphLaunch(exec, s);
+    } else {
+        e = enqueue(p, f, Q, Qim, s);
     }
     if (e) {
         p->dirty = true;
         return cuda_fail((cudaError_t)e, "collision launch");
     }
     return WKE_OK;
-}
-
-int collision(wke_plan *p, const void *f, void *Q, void *Qim, cudaStream_t s) {
-    return p->hp.precision == WKE_FP32 ? collision_T<float>(p, f, Q, Qim, s) : collision_T<double>(p, f, Q, Qim, s);
 }
 
 }  // namespace
@@ -257,8 +352,9 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         field = static_cast<decltype(field)>(ptr);           \
     } while (0)
     ALLOC(p->dp.ghat, nd * cxb);
-    ALLOC(p->dp.H, std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
-    p->dp.fwd_tmp = p->dp.H;
+    ALLOC(p->Hbuf[0], std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
+    ALLOC(p->Hbuf[1], std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
+    p->dp.H = p->dp.fwd_tmp = p->Hbuf[0];
     ALLOC(p->dp.Qacc, (size_t)hp.groups_per_chunk * nd * 8);
     ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
     ALLOC(p->dp.phase, nf * hp.d * hp.N * cxb);
@@ -275,6 +371,16 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
 #undef ALLOC
     rc = hp.precision == WKE_FP32 ? upload_tables<float>(p) : upload_tables<double>(p);
     if (rc) goto error;
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->s1, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&p->ev_fork, &p->ev_join, &p->ev_p1[0], &p->ev_p1[1], &p->ev_p2[0], &p->ev_p2[1]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "stream and event creation");
+            goto error;
+        }
+    }
     if ((rc = clear_accumulators(p, nullptr))) goto error;
     {
         cudaError_t e = cudaDeviceSynchronize();
@@ -409,6 +515,13 @@ int wke_moments(wke_plan *plan, const void *g, double *out, void *stream) {
     int e = plan->hp.precision == WKE_FP32 ? moments_T<float>(plan->hp, g, plan->mom_partials, out, s)
                                            : moments_T<double>(plan->hp, g, plan->mom_partials, out, s);
     if (e) return cuda_fail((cudaError_t)e, "moments");
+    return WKE_OK;
+}
+
+int wke_plan_use_graphs(wke_plan *plan, int enable) {
+    if (!plan) return fail(WKE_ERR_INVALID, "plan is NULL");
+    plan->use_graphs = enable != 0;
+    if (!plan->use_graphs) free_graphs(plan);
     return WKE_OK;
 }
 

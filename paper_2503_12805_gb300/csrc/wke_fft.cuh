@@ -135,14 +135,31 @@ template <int N> struct LinePad {
     static constexpr int PITCH = LEN + ((4 - (LEN % 16)) + 16) % 16;
 };
 
-template <typename T, int N, int E, int DIR, int NS> struct LineStages {
+// Scratch policies.  WarpScratch: the line's threads are lanes of one warp
+// and its scratch is contiguous (padded); exchanges need only __syncwarp.
+// ColScratch: a block transforms many lines ("columns") at once, column z's
+// point pos lives at (pad(pos)) * ld + z, so a warp of consecutive columns
+// touches consecutive words; exchanges need __syncthreads.
+template <typename T, int N> struct WarpScratch {
+    cx<T> *base;
+    __device__ __forceinline__ cx<T> &at(int pos) const { return base[LinePad<N>::at(pos)]; }
+    __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
+template <typename T, int N> struct ColScratch {
+    cx<T> *base;   // already offset by the column index
+    int ld;        // columns of the scratch
+    __device__ __forceinline__ cx<T> &at(int pos) const { return base[(size_t)LinePad<N>::at(pos) * ld]; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+
+template <typename T, int N, int E, int DIR, int NS, class S> struct LineStages {
     static constexpr int TPL = N / E;
     static constexpr int R = ce_min(N / NS, E);
     static constexpr int B = E / R;              // butterflies per thread
     static constexpr bool LAST = (NS * R == N);
     static_assert(E % R == 0, "radix must divide the points per thread");
 
-    __device__ __forceinline__ static void run(cx<T> (&v)[E], int t, cx<T> *scr, const cx<T> *tw) {
+    __device__ __forceinline__ static void run(cx<T> (&v)[E], int t, const S &scr, const cx<T> *tw) {
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int j = t + u * TPL;
@@ -165,28 +182,38 @@ template <typename T, int N, int E, int DIR, int NS> struct LineStages {
             } else {
                 const int base = (j / NS) * NS * R + jm;
 #pragma unroll
-                for (int r = 0; r < R; ++r) scr[LinePad<N>::at(base + r * NS)] = bf[r];
+                for (int r = 0; r < R; ++r) scr.at(base + r * NS) = bf[r];
             }
         }
         if (!LAST) {
-            __syncwarp();
+            S::sync();
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = scr[LinePad<N>::at(t + e * TPL)];
-            __syncwarp();
-            LineStages<T, N, E, DIR, (LAST ? N : NS * R)>::run(v, t, scr, tw);
+            for (int e = 0; e < E; ++e) v[e] = scr.at(t + e * TPL);
+            S::sync();
+            LineStages<T, N, E, DIR, NS * R, S>::run(v, t, scr, tw);
         }
     }
 };
 
-template <typename T, int N, int E, int DIR> struct LineStages<T, N, E, DIR, N> {
-    __device__ __forceinline__ static void run(cx<T> (&)[E], int, cx<T> *, const cx<T> *) {}
+template <typename T, int N, int E, int DIR, class S> struct LineStages<T, N, E, DIR, N, S> {
+    __device__ __forceinline__ static void run(cx<T> (&)[E], int, const S &, const cx<T> *) {}
 };
 
 // Transform one line held as described above.  `scr` is this line's scratch
 // (LinePad<N>::LEN slots), `tw` the table exp(+2 pi i k / N), k < N.
 template <typename T, int N, int E, int DIR>
 __device__ __forceinline__ void line_fft(cx<T> (&v)[E], int t, cx<T> *scr, const cx<T> *tw) {
-    LineStages<T, N, E, DIR, 1>::run(v, t, scr, tw);
+    WarpScratch<T, N> s{scr};
+    LineStages<T, N, E, DIR, 1, WarpScratch<T, N>>::run(v, t, s, tw);
+}
+
+// Transform the column `z` of a block-wide set of columns: thread t of the
+// column holds points t + e * (N / E); `scr` has LinePad<N>::LEN rows of
+// `ld` columns.  Every thread of the block must call this together.
+template <typename T, int N, int E, int DIR>
+__device__ __forceinline__ void col_fft(cx<T> (&v)[E], int t, cx<T> *scr, int z, int ld, const cx<T> *tw) {
+    ColScratch<T, N> s{scr + z, ld};
+    LineStages<T, N, E, DIR, 1, ColScratch<T, N>>::run(v, t, s, tw);
 }
 
 // Points per thread by precision and length.

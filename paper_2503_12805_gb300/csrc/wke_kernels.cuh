@@ -42,7 +42,8 @@ __device__ __forceinline__ void load_twiddles(cx<T> *tw, const cx<T> *tw_g) {
 
 // ------------------------------------------------------------------ forward
 // 3D: forward transform over axes (1, 2) of every plane i1 of the real input,
-// in double.  One block per plane, one warp-line per row / column.
+// in double.  One block per plane: row lines along axis 2, then column lines
+// along axis 1 with consecutive columns per warp (coalesced stores).
 template <typename TIn, int N>
 __global__ void __launch_bounds__(N * LineCfg<double, N>::TPL)
 k_fwd_planes_3d(const TIn *__restrict__ f, double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
@@ -55,23 +56,24 @@ k_fwd_planes_3d(const TIn *__restrict__ f, double2 *__restrict__ tmp, const doub
     load_twiddles<double, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
-    const int line = warp * LPW + c;
-    double2 *scr = scratch + (size_t)line * LinePad<N>::PITCH;
+    const int row = warp * LPW + c;
+    const int z = threadIdx.x % N, ty = threadIdx.x / N;
+    double2 *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
     const int i1 = blockIdx.x;
-    const TIn *row = f + ((size_t)i1 * N + line) * N;
+    const TIn *src = f + ((size_t)i1 * N + row) * N;
     double2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = make_double2((double)row[t + e * TPL], 0.0);
-    line_fft<double, N, E, -1>(v, t, scr, tw);
+    for (int e = 0; e < E; ++e) v[e] = make_double2((double)src[t + e * TPL], 0.0);
+    line_fft<double, N, E, -1>(v, t, rscr, tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) work[line * WP + t + e * TPL] = v[e];
+    for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = work[(t + e * TPL) * WP + line];
-    line_fft<double, N, E, -1>(v, t, scr, tw);
+    for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
+    col_fft<double, N, E, -1>(v, ty, scratch, z, N, tw);
     double2 *out = tmp + (size_t)i1 * N * N;
 #pragma unroll
-    for (int e = 0; e < E; ++e) out[(t + e * TPL) * N + line] = v[e];
+    for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
 }
 
 // 2D: forward transform of every row, in double.
@@ -135,9 +137,11 @@ __global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict
 
 // ------------------------------------------------------------------ pass 1
 // 3D: block (j1, field block).  For each field of the block: row lines take
-// the phase-weighted spectrum of plane j1 and transform along axis 2, a
-// shared-memory transpose hands columns to the same warps for axis 1, and
-// the result goes to H[field][j1][y][z].
+// the phase-weighted spectrum of plane j1 and transform along axis 2 (one
+// warp per LPW rows); the rows go through shared memory; then every column
+// z is transformed along axis 1 by N/8 threads spread over the block, with
+// 32 consecutive columns per warp, so the stores to H[field][j1][y][z] are
+// whole 256-byte rows.
 template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
 k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
@@ -147,36 +151,37 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *work = tw + N;
-    cx<T> *scratch = work + N * WP;
+    cx<T> *scratch = work + N * WP;           // row scratch, then column scratch
     load_twiddles<T, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
-    const int line = warp * LPW + c;
-    cx<T> *scr = scratch + (size_t)line * LinePad<N>::PITCH;
+    const int row = warp * LPW + c;           // axis-1 index j2 of this row line
+    const int z = threadIdx.x % N, ty = threadIdx.x / N;   // column lines
+    cx<T> *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
     const int j1 = blockIdx.x;
     const int fbeg = blockIdx.y * fields_per_block;
     const int fend = min(nfields, fbeg + fields_per_block);
     const size_t NN = (size_t)N * N;
-    const cx<T> *grow = ghat + ((size_t)j1 * N + line) * N;
+    const cx<T> *grow = ghat + ((size_t)j1 * N + row) * N;
     cx<T> g[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) g[e] = grow[t + e * TPL];
     for (int fl = fbeg; fl < fend; ++fl) {
         const cx<T> *ph = phase + (size_t)(field0 + fl) * 3 * N;
-        const cx<T> p01 = cmul<T>(ph[j1], ph[N + line]);
+        const cx<T> p01 = cmul<T>(ph[j1], ph[N + row]);
         cx<T> v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cmul<T>(cmul<T>(g[e], ph[2 * N + t + e * TPL]), p01);
-        line_fft<T, N, E, +1>(v, t, scr, tw);
+        line_fft<T, N, E, +1>(v, t, rscr, tw);
 #pragma unroll
-        for (int e = 0; e < E; ++e) work[line * WP + t + e * TPL] = v[e];
+        for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = work[(t + e * TPL) * WP + line];
-        line_fft<T, N, E, +1>(v, t, scr, tw);
+        for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
+        col_fft<T, N, E, +1>(v, ty, scratch, z, N, tw);
         cx<T> *out = H + ((size_t)fl * N + j1) * NN;
 #pragma unroll
-        for (int e = 0; e < E; ++e) out[(t + e * TPL) * N + line] = v[e];
+        for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
         __syncthreads();
     }
 }
@@ -211,38 +216,51 @@ __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restri
 }
 
 // ------------------------------------------------------------------ pass 2
-// Block (column tile, group of the chunk).  Each warp-line owns one column
-// of the trailing axes: it transforms C once, then for every product of the
-// group A and B, and accumulates W [A B (C + F) - C F (A + B)] for its N
-// points; the group's sum is added to that group's double accumulator.
+// Block (column tile, group of the chunk).  A tile is CB consecutive columns
+// of the trailing axes; each column's N points along axis 0 are held by
+// TPL = N/E threads spread over the block (thread ty holds points
+// ty + e TPL), so every warp reads and writes 32 consecutive columns of one
+// row.  The block transforms C once and keeps s = C + F and cf = C F; for
+// every product of the group it transforms A, forms X = A s - cf and adds
+// the term -cf A, then transforms B and adds B X, since
+// A B (C + F) - C F (A + B) = B (A s - cf) - cf A.  Only one transformed
+// field is live at a time.  The group's sum goes to that group's double
+// accumulator.
+template <typename T, int N> struct Pass2Cfg {
+    static constexpr int E = N <= 64 ? 4 : 8;           // points per thread
+    static constexpr int TPL = N / E;                    // threads per column
+    static constexpr int THREADS = 256;
+    static constexpr int CB = THREADS / TPL;             // columns per block (at most)
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? (E == 4 ? 3 : 2) : (E == 4 ? 2 : 1);
+};
+
 template <typename T, int N, bool IM>
-__global__ void k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ f, double *__restrict__ Qacc,
-                        double *__restrict__ Qim, const int *__restrict__ prod_local,
-                        const double *__restrict__ prod_W, const cx<T> *__restrict__ tw_g, int P, int FPG,
-                        int PPG, int g0) {
-    typedef LineCfg<T, N> Cfg;
-    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
+__global__ void __launch_bounds__(Pass2Cfg<T, N>::THREADS, Pass2Cfg<T, N>::MIN_BLOCKS)
+k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
+        const int *__restrict__ prod_local, const double *__restrict__ prod_W, const cx<T> *__restrict__ tw_g, int P,
+        int CB, int FPG, int PPG, int g0) {
+    typedef Pass2Cfg<T, N> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *scratch = tw + N;
+    cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
     load_twiddles<T, N>(tw, tw_g);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = lane % LPW, t = lane / LPW;
-    const int wl = warp * LPW + c;
-    const int col = blockIdx.x * (blockDim.x / 32) * LPW + wl;
+    const int z = threadIdx.x % CB, t = threadIdx.x / CB;
+    const int col = blockIdx.x * CB + z;
     const int gl = blockIdx.y;
-    cx<T> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     const size_t ND = (size_t)N * P;
     const cx<T> *Hg = H + (size_t)gl * FPG * ND;
 
-    cx<T> C[E];
+    cx<T> v[E], s[E], cf[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) C[e] = Hg[(size_t)(t + e * TPL) * P + col];
-    line_fft<T, N, E, +1>(C, t, scr, tw);
-    T F[E], ar[E], ai[E];
+    for (int e = 0; e < E; ++e) v[e] = Hg[(size_t)(t + e * TPL) * P + col];
+    col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
+    T ar[E], ai[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        F[e] = f[(size_t)(t + e * TPL) * P + col];
+        const T F = f[(size_t)(t + e * TPL) * P + col];
+        s[e] = mkc<T>(v[e].x + F, v[e].y);
+        cf[e] = mkc<T>(v[e].x * F, v[e].y * F);
         ar[e] = (T)0;
         ai[e] = (T)0;
     }
@@ -251,39 +269,33 @@ __global__ void k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ f, do
         const cx<T> *HA = Hg + (size_t)prod_local[2 * p] * ND;
         const cx<T> *HB = Hg + (size_t)prod_local[2 * p + 1] * ND;
         const T W = (T)Wg[p];
-        cx<T> A[E], B[E];
+        cx<T> X[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = HA[(size_t)(t + e * TPL) * P + col];
+        col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            A[e] = HA[(size_t)(t + e * TPL) * P + col];
-            B[e] = HB[(size_t)(t + e * TPL) * P + col];
+            X[e] = csub<T>(cmul<T>(v[e], s[e]), cf[e]);
+            const cx<T> q = cmul<T>(cf[e], v[e]);            // added with a minus sign
+            ar[e] -= W * q.x;
+            if (IM) ai[e] -= W * q.y;
         }
-        line_fft<T, N, E, +1>(A, t, scr, tw);
-        line_fft<T, N, E, +1>(B, t, scr, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = HB[(size_t)(t + e * TPL) * P + col];
+        col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            // K1 - K2 + K3 - K4 = A B (C + F) - C F (A + B)
-            const cx<T> ab = cmul<T>(A[e], B[e]);
-            const cx<T> cf = mkc<T>(C[e].x * F[e], C[e].y * F[e]);
-            const cx<T> cpf = mkc<T>(C[e].x + F[e], C[e].y);
-            const cx<T> apb = cadd<T>(A[e], B[e]);
-            const cx<T> pr = csub<T>(cmul<T>(ab, cpf), cmul<T>(cf, apb));
-            ar[e] += W * pr.x;
-            if (IM) ai[e] += W * pr.y;
+            ar[e] += W * (v[e].x * X[e].x - v[e].y * X[e].y);
+            if (IM) ai[e] += W * (v[e].x * X[e].y + v[e].y * X[e].x);
         }
     }
     double *Qg = Qacc + (size_t)gl * ND;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const size_t idx = (size_t)(t + e * TPL) * P + col;
-        Qg[idx] += (double)ar[e];
-    }
+    for (int e = 0; e < E; ++e) Qg[(size_t)(t + e * TPL) * P + col] += (double)ar[e];
     if (IM) {
         double *Qig = Qim + (size_t)gl * ND;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const size_t idx = (size_t)(t + e * TPL) * P + col;
-            Qig[idx] += (double)ai[e];
-        }
+        for (int e = 0; e < E; ++e) Qig[(size_t)(t + e * TPL) * P + col] += (double)ai[e];
     }
 }
 

@@ -13,7 +13,11 @@ template <typename K> static int set_smem(K kernel, size_t bytes) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return (int)e;
     }
-    return 0;
+    // prefer the largest shared-memory carveout so that shared memory never
+    // limits the blocks per SM below what registers allow
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    return (int)e;
 }
 
 static inline size_t nd_of(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
@@ -89,16 +93,16 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
 // ------------------------------------------------------------------ pass 2
 template <typename T, int N, bool IM>
 static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
-    typedef LineCfg<T, N> Cfg;
+    typedef Pass2Cfg<T, N> Cfg;
     const int P = cols_of(hp);
-    const int warps = line_warps<T, N>(P);
-    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
+    const int CB = std::min(Cfg::CB, P);       // columns per block
+    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB) * sizeof(cx<T>);
     int rc = 0;
     if ((rc = set_smem(k_pass2<T, N, IM>, smem))) return rc;
-    dim3 grid(P / (warps * Cfg::LPW), ng);
-    k_pass2<T, N, IM><<<grid, warps * 32, smem, s>>>(
+    dim3 grid(P / CB, ng);
+    k_pass2<T, N, IM><<<grid, CB * Cfg::TPL, smem, s>>>(
         static_cast<const cx<T> *>(p.H), static_cast<const T *>(p.f), p.Qacc, p.Qacc_im, p.prod_local, p.prod_W,
-        static_cast<const cx<T> *>(p.tw), P, hp.fields_per_group, hp.products_per_group, g0);
+        static_cast<const cx<T> *>(p.tw), P, CB, hp.fields_per_group, hp.products_per_group, g0);
     return (int)cudaGetLastError();
 }
 

@@ -354,7 +354,7 @@ size_t plan_device_bytes(const HostPlan &hp) {
     size_t n_fields = (size_t)hp.n_groups * hp.fields_per_group;
     size_t bytes = 0;
     bytes += nd * cxb;                                                  // ghat
-    bytes += std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16);  // H
+    bytes += 2 * std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16);  // H x 2
     bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
     bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles

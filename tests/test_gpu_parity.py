@@ -225,3 +225,21 @@ def test_host_buffer_call_matches_device_call():
         qh = torch.empty_like(fh).pin_memory()
         plan.collision_host(fh, qh)
     assert np.array_equal(qh.double().numpy(), dev)
+
+
+def test_graph_replay_matches_direct_launches():
+    """The cached CUDA graph of an evaluation replays exactly the kernels the
+    direct path launches; several pointer sets share one plan."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    fs = [I.ring(3, 32, 8.0), I.gaussian_noise(3, 32, 8.0, 77, 0.1)]
+    with _plan(wke, 3, 32, 8.0, 4, 8, 8, "cube", precision="fp32", chunk_bytes=2 << 20) as plan:
+        assert plan.info().n_chunks > 2            # exercises both intermediate buffers
+        ft = [torch.tensor(f, dtype=torch.float32, device="cuda") for f in fs]
+        graph = [[plan.collision(f) for f in ft] for _ in range(2)]
+        wke.wke_plan_use_graphs(plan.handle, False)
+        direct = [plan.collision(f) for f in ft]
+        torch.cuda.synchronize()
+    for g_rep in graph:
+        for a, b in zip(g_rep, direct):
+            assert torch.equal(a, b)
