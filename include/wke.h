@@ -204,6 +204,22 @@ int wke_plan_use_graphs(wke_plan *plan, int enable);
 int wke_plan_profile(wke_plan *plan, int enable);
 int wke_plan_profile_read(wke_plan *plan, double *out_host);
 
+/* The same sums as wke_moments for callers that cannot allocate device
+ * memory where they need them (a caller living inside another allocator's
+ * fixed budget, or one that must not allocate while a stream capture is
+ * open): no plan, no cudaMalloc, no cudaFree.  The paper has no counterpart;
+ * this is a service of the library.  d in {2, 3}, grid N^d on [-L, L]^d as
+ * above, precision WKE_FP64 (g is double) or WKE_FP32 (g is float);
+ * out_dev receives d + 2 doubles; asynchronous on `stream`.
+ * The per-block partial sums live in a fixed 40 KiB array in the library's
+ * device image, so grids above 4,194,304 points (1024 blocks of 4096) are
+ * rejected with WKE_ERR_INVALID.  The first call on each device resolves the
+ * array's address with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU race, so order them (one stream, or events). */
+int wke_moments_noalloc(int d, int N, double L, int precision, const void *g_dev, double *out_dev,
+                        void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *wke_last_error_string(void);
 

@@ -63,7 +63,7 @@ EXPORTED = [
     "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
     "wke_plan_get_info", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
-    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
+    "wke_moments_noalloc", "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
 ]
 PROF_CLASSES = ("forward", "pass1", "pass2", "finalize")
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_plan_set_stream": (i, [vp, vp]),
         "wke_step": (i, [vp, vp, d, i]),
         "wke_moments": (i, [vp, vp, vp, vp]),
+        "wke_moments_noalloc": (i, [i, i, d, i, vp, vp, vp]),
         "wke_plan_use_graphs": (i, [vp, i]),
         "wke_plan_profile": (i, [vp, i]),
         "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
@@ -173,6 +174,13 @@ def wke_step(plan, f_ptr: int, dt: float, rk_stages: int) -> None:
 
 def wke_moments(plan, g_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _check(lib().wke_moments(plan, g_ptr, out_ptr, stream))
+
+
+def wke_moments_noalloc(d: int, N: int, L: float, precision: int, g_ptr: int, out_ptr: int,
+                        stream: int = 0) -> None:
+    """Plan-free moments for callers that cannot allocate device memory; the
+    partial sums live in a fixed array inside the library (see wke.h)."""
+    _check(lib().wke_moments_noalloc(d, N, L, precision, g_ptr, out_ptr, stream))
 
 
 def wke_plan_use_graphs(plan, enable: bool) -> None:
