@@ -283,18 +283,21 @@ def run_gpu(args, rank, world, pool, workers):
 
 def kernel_flops(cls, info):
     """Algorithmic flops of one launch of a kernel class (the arithmetic the
-    executed algorithm needs: 5 n log2 n per complex n-point transform, two
-    complex products per point for the phases, 30 per point per product)."""
+    executed algorithm needs: 5 n log2 n per complex n-point transform, 16 per
+    point for the two phase products and the packing of a unit, 30 per point
+    per product).  A unit is two shifted fields packed in one transform."""
     d, N, G = info.d, info.N, info.groups_per_chunk
     nd = N ** d
     P = nd // N
-    fpg, ppg = info.fields_per_group, info.products_per_group
+    ppg = info.products_per_group
+    units = (G + 1) // 2 + G * ppg
     if cls == "pass1":
-        per_field = N * (5.0 * P * math.log2(P) + 12.0 * P)
-        return G * fpg * per_field
+        return units * N * (5.0 * P * math.log2(P) + 16.0 * P)
     if cls == "pass2":
-        per_group = (1 + 2 * ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
+        per_group = (1 + ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
         return G * per_group
+    if cls == "nyquist":
+        return G * info.fields_per_group * d * 5.0 * P * math.log2(P)
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * G * nd

@@ -198,9 +198,11 @@ int wke_plan_use_graphs(wke_plan *plan, int enable);
  * wke_plan_profile_read() must be called after that stream is idle: it adds
  * up the recorded intervals per kernel class into out_host[2 * WKE_PROF_CLASSES]
  * as (total milliseconds, number of launches) pairs, in the order forward,
- * pass 1, pass 2, finalize, and forgets them.  Enabling resets the record.
- * While enabled, evaluations launch directly (no graph replay). */
-#define WKE_PROF_CLASSES 4
+ * pass 1, pass 2, finalize, Nyquist tables, and forgets them.  Enabling resets the record.
+ * While enabled, evaluations launch directly (no graph replay) and the two
+ * passes of consecutive chunks do not overlap, so each interval is one
+ * kernel's own duration. */
+#define WKE_PROF_CLASSES 5
 int wke_plan_profile(wke_plan *plan, int enable);
 int wke_plan_profile_read(wke_plan *plan, double *out_host);
 

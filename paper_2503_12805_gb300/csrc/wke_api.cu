@@ -15,6 +15,7 @@ const char *last_error();
 
 template <typename T> int forward_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
 template <typename T> int pass1_T(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);
+template <typename T> int nyquist_T(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);
 template <typename T> int pass2_T(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);
 template <typename T> int finalize_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
 template <typename T> int moments_T(const HostPlan &, const void *, double *, double *, cudaStream_t);
@@ -44,6 +45,7 @@ struct wke_plan {
     HostPlan hp;
     DevicePtrs dp{};
     void *Hbuf[2] = {nullptr, nullptr};   // double-buffered chunk intermediates
+    void *Vbuf[2] = {nullptr, nullptr};   // double-buffered chunk Nyquist tables
     // pass 1 of chunk c+1 runs on s1 while pass 2 of chunk c runs on s2
     cudaStream_t s1 = nullptr, s2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
@@ -207,7 +209,9 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
     dp.f = f;
     dp.H = p->Hbuf[0];
     dp.fwd_tmp = p->Hbuf[0];
-    cudaStream_t s1 = p->s1, s2 = p->s2;
+    // while profiling, both passes share one stream so that each launch's
+    // interval measures that kernel alone
+    cudaStream_t s1 = p->s1, s2 = p->profiling ? p->s1 : p->s2;
     int e = (int)cudaEventRecord(p->ev_fork, origin);
     if (!e) e = (int)cudaStreamWaitEvent(s1, p->ev_fork, 0);
     if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_fork, 0);
@@ -220,7 +224,12 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         const int ng = std::min(hp.groups_per_chunk, hp.n_groups - g0);
         const int buf = c & 1;
         dp.H = p->Hbuf[buf];
+        dp.V = p->Vbuf[buf];
         if (c >= 2) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
+        if (!e && hp.nyquist == WKE_NYQ_KEEP) {
+            ProfScope ps(p, s1, 4);
+            e = nyquist_T<T>(hp, dp, g0, ng, s1);
+        }
         if (!e) {
             ProfScope ps(p, s1, 1);
             e = pass1_T<T>(hp, dp, g0, ng, s1);
@@ -352,8 +361,11 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         field = static_cast<decltype(field)>(ptr);           \
     } while (0)
     ALLOC(p->dp.ghat, nd * cxb);
-    ALLOC(p->Hbuf[0], std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
-    ALLOC(p->Hbuf[1], std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16));
+    ALLOC(p->dp.nslice, (size_t)hp.d * (nd / hp.N) * cxb);
+    ALLOC(p->Hbuf[0], chunk_unit_bytes(hp));
+    ALLOC(p->Hbuf[1], chunk_unit_bytes(hp));
+    ALLOC(p->Vbuf[0], chunk_v_bytes(hp));
+    ALLOC(p->Vbuf[1], chunk_v_bytes(hp));
     p->dp.H = p->dp.fwd_tmp = p->Hbuf[0];
     ALLOC(p->dp.Qacc, (size_t)hp.groups_per_chunk * nd * 8);
     ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
@@ -416,7 +428,7 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     info->products_per_group = hp.products_per_group;
     info->groups_per_chunk = hp.groups_per_chunk;
     info->n_chunks = hp.n_chunks;
-    info->launches_per_collision = 2 + 2 * hp.n_chunks + 1;
+    info->launches_per_collision = 2 + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1;
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
     info->device_bytes = plan->bytes;

@@ -41,7 +41,12 @@ struct HostPlan {
     std::vector<int> prod_fa, prod_fb;   // products_per_group local field ids
     std::vector<double> prod_W;          // n_groups * products_per_group weights
 
-    // Chunking of groups through the intermediate buffer.
+    // Chunking of groups through the intermediate buffer.  Pass 1 transforms
+    // "units": two shifted fields packed as one complex transform of
+    // ghat (E_a + i E_b).  A chunk of ng groups has ceil(ng / 2) C units (the
+    // C fields of groups 2k and 2k+1 together; a lone C when ng is odd)
+    // followed by ng * products_per_group product units (fields fa, fb of
+    // each product).
     int groups_per_chunk = 0, n_chunks = 0;
     size_t chunk_bytes = 0;
 
@@ -70,7 +75,9 @@ struct DevicePtrs {
     const void *f;            // input grid (T)
     void *ghat;               // N^d complex T: coefficients of f (DFT order)
     void *fwd_tmp;            // N^d complex double: forward-transform scratch
-    void *H;                  // chunk intermediate fields, complex T
+    void *H;                  // chunk intermediate units, complex T
+    void *V;                  // chunk Nyquist tables, real T: per field, d tables of N^{d-1}
+    void *nslice;             // d masked Nyquist slices of ghat, N^{d-1} complex T each
     double *Qacc;             // groups_per_chunk * N^d partial sums (real)
     double *Qacc_im;          // groups_per_chunk * N^d partial sums (imag) or null
     const void *phase;        // n_fields * d * N complex T phase tables
@@ -79,6 +86,11 @@ struct DevicePtrs {
     const int *prod_local;    // products_per_group * 2 ints (fa, fb)
     const double *prod_W;     // n_groups * products_per_group
 };
+
+// Units of a chunk of ng groups (C units first, then product units).
+inline int chunk_units(const HostPlan &hp, int ng) { return (ng + 1) / 2 + ng * hp.products_per_group; }
+size_t chunk_unit_bytes(const HostPlan &hp);   // H buffer bytes for a full chunk
+size_t chunk_v_bytes(const HostPlan &hp);      // V buffer bytes for a full chunk
 
 int launch_forward(const HostPlan &hp, const DevicePtrs &p, void *stream);
 int launch_pass1(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);

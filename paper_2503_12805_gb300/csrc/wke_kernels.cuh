@@ -100,9 +100,14 @@ __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, double2 *__restrict__ t
 
 // Both d: forward transform along axis 0 of every column; writes
 // ghat = DFT / N^d in T, optionally zeroing modes with a component -N/2.
+// When `nslice` is not null it also receives the Nyquist slices used by the
+// Nyquist tables: slice ax holds the modes with j_ax = -N/2 (position N/2),
+// indexed by the other axes in increasing order, with the modes that have an
+// earlier axis at -N/2 set to zero (so the slices are disjoint).
 template <typename TOut, int N>
 __global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict__ ghat,
-                           const double2 *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero) {
+                           const double2 *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero,
+                           cx<TOut> *__restrict__ nslice) {
     typedef LineCfg<double, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,21 +136,62 @@ __global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict
         const int j1 = t + e * TPL;
         double2 x = v[e];
         if (nyq_zero && (col_nyq || j1 == N / 2)) x = make_double2(0.0, 0.0);
-        ghat[(size_t)j1 * P + col] = mkc<TOut>((TOut)(x.x * inv_nd), (TOut)(x.y * inv_nd));
+        const cx<TOut> val = mkc<TOut>((TOut)(x.x * inv_nd), (TOut)(x.y * inv_nd));
+        ghat[(size_t)j1 * P + col] = val;
+        if (nslice) {
+            const cx<TOut> zero = mkc<TOut>((TOut)0, (TOut)0);
+            constexpr int H2 = N / 2;
+            if (d == 3) {
+                const int j2 = col / N, j3 = col - j2 * N;
+                if (j1 == H2) nslice[(size_t)j2 * N + j3] = val;
+                if (j2 == H2) nslice[(size_t)N * N + (size_t)j1 * N + j3] = j1 == H2 ? zero : val;
+                if (j3 == H2) nslice[(size_t)2 * N * N + (size_t)j1 * N + j2] = (j1 == H2 || j2 == H2) ? zero : val;
+            } else {
+                if (j1 == H2) nslice[col] = val;
+                if (col == H2) nslice[N + j1] = j1 == H2 ? zero : val;
+            }
+        }
     }
 }
 
 // ------------------------------------------------------------------ pass 1
-// 3D: block (j1, field block).  For each field of the block: row lines take
-// the phase-weighted spectrum of plane j1 and transform along axis 2 (one
-// warp per LPW rows); the rows go through shared memory; then every column
-// z is transformed along axis 1 by N/8 threads spread over the block, with
-// 32 consecutive columns per warp, so the stores to H[field][j1][y][z] are
-// whole 256-byte rows.
+// Global field indices (fa, fb) of unit u of the chunk starting at group g0
+// with ng groups; fb = -1 for a lone C unit.
+__device__ __forceinline__ void unit_fields(int u, int g0, int ng, int FPG, int PPG, const int *__restrict__ prod_local,
+                                            int &fa, int &fb) {
+    const int ncu = (ng + 1) >> 1;
+    if (u < ncu) {
+        const int ga = g0 + 2 * u;
+        fa = ga * FPG;
+        fb = 2 * u + 1 < ng ? (ga + 1) * FPG : -1;
+    } else {
+        const int k = u - ncu;
+        const int gl = k / PPG, p = k - gl * PPG;
+        fa = (g0 + gl) * FPG + prod_local[2 * p];
+        fb = (g0 + gl) * FPG + prod_local[2 * p + 1];
+    }
+}
+
+// ghat(j) (E_a(j) + i E_b(j)) for one point, with E_x = row factor * tab[j]:
+// the packed spectrum of the unit (fields a and b real up to their Nyquist
+// parts, see pass 2).
+template <typename T>
+__device__ __forceinline__ cx<T> packed(cx<T> g, cx<T> ea, cx<T> eb) {
+    const cx<T> e = mkc<T>(ea.x - eb.y, ea.y + eb.x);
+    return cmul<T>(g, e);
+}
+
+// 3D: block (j1, unit block).  For each unit of the block: row lines take the
+// packed spectrum of plane j1 and transform along axis 2 (one warp per LPW
+// rows); the rows go through shared memory; then every column z is
+// transformed along axis 1 by N/8 threads spread over the block, with 32
+// consecutive columns per warp, so the stores to H[unit][j1][y][z] are whole
+// rows.
 template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
 k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
-           const cx<T> *__restrict__ tw_g, int field0, int nfields, int fields_per_block) {
+           const cx<T> *__restrict__ tw_g, const int *__restrict__ prod_local, int g0, int ng, int FPG, int PPG,
+           int nunits, int units_per_block) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,20 +204,32 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     const int row = warp * LPW + c;           // axis-1 index j2 of this row line
     const int z = threadIdx.x % N, ty = threadIdx.x / N;   // column lines
     cx<T> *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
-    const int j1 = blockIdx.x;
-    const int fbeg = blockIdx.y * fields_per_block;
-    const int fend = min(nfields, fbeg + fields_per_block);
+    const int ubeg = blockIdx.y * units_per_block;
+    const int uend = min(nunits, ubeg + units_per_block);
     const size_t NN = (size_t)N * N;
+    const int j1 = blockIdx.x;
     const cx<T> *grow = ghat + ((size_t)j1 * N + row) * N;
     cx<T> g[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) g[e] = grow[t + e * TPL];
-    for (int fl = fbeg; fl < fend; ++fl) {
-        const cx<T> *ph = phase + (size_t)(field0 + fl) * 3 * N;
-        const cx<T> p01 = cmul<T>(ph[j1], ph[N + row]);
+    for (int u = ubeg; u < uend; ++u) {
+        int fa, fb;
+        unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+        const cx<T> *pa = phase + (size_t)fa * 3 * N;
+        const cx<T> a01 = cmul<T>(pa[j1], pa[N + row]);
         cx<T> v[E];
+        if (fb >= 0) {
+            const cx<T> *pb = phase + (size_t)fb * 3 * N;
+            const cx<T> b01 = cmul<T>(pb[j1], pb[N + row]);
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cmul<T>(cmul<T>(g[e], ph[2 * N + t + e * TPL]), p01);
+            for (int e = 0; e < E; ++e) {
+                const int j3 = t + e * TPL;
+                v[e] = packed<T>(g[e], cmul<T>(pa[2 * N + j3], a01), cmul<T>(pb[2 * N + j3], b01));
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = cmul<T>(g[e], cmul<T>(pa[2 * N + t + e * TPL], a01));
+        }
         line_fft<T, N, E, +1>(v, t, rscr, tw);
 #pragma unroll
         for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
@@ -179,18 +237,19 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
         col_fft<T, N, E, +1>(v, ty, scratch, z, N, tw);
-        cx<T> *out = H + ((size_t)fl * N + j1) * NN;
+        cx<T> *out = H + ((size_t)u * N + j1) * NN;
 #pragma unroll
         for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
         __syncthreads();
     }
 }
 
-// 2D: block (row block, field).  Row j1 of the phase-weighted spectrum,
-// inverse transform along axis 1 -> H[field][j1][y].
+// 2D: block (row block, unit).  Row j1 of the packed spectrum, inverse
+// transform along axis 1 -> H[unit][j1][y].
 template <typename T, int N>
 __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
-                           const cx<T> *__restrict__ tw_g, int field0) {
+                           const cx<T> *__restrict__ tw_g, const int *__restrict__ prod_local, int g0, int ng,
+                           int FPG, int PPG) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,18 +260,150 @@ __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restri
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
     const int j1 = blockIdx.x * (blockDim.x / 32) * LPW + wl;
-    const int fl = blockIdx.y;
+    const int u = blockIdx.y;
     cx<T> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
-    const cx<T> *ph = phase + (size_t)(field0 + fl) * 2 * N;
-    const cx<T> p0 = ph[j1];
+    int fa, fb;
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    const cx<T> *pa = phase + (size_t)fa * 2 * N;
+    const cx<T> a0 = pa[j1];
     cx<T> v[E];
+    if (fb >= 0) {
+        const cx<T> *pb = phase + (size_t)fb * 2 * N;
+        const cx<T> b0 = pb[j1];
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-        v[e] = cmul<T>(cmul<T>(ghat[(size_t)j1 * N + t + e * TPL], ph[N + t + e * TPL]), p0);
+        for (int e = 0; e < E; ++e) {
+            const int j2 = t + e * TPL;
+            v[e] = packed<T>(ghat[(size_t)j1 * N + j2], cmul<T>(pa[N + j2], a0), cmul<T>(pb[N + j2], b0));
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            v[e] = cmul<T>(ghat[(size_t)j1 * N + t + e * TPL], cmul<T>(pa[N + t + e * TPL], a0));
+    }
     line_fft<T, N, E, +1>(v, t, scr, tw);
-    cx<T> *out = H + ((size_t)fl * N + j1) * N;
+    cx<T> *out = H + ((size_t)u * N + j1) * N;
 #pragma unroll
     for (int e = 0; e < E; ++e) out[t + e * TPL] = v[e];
+}
+
+// ------------------------------------------------------------------ Nyquist tables
+// For field x and axis ax, the modes with j_ax = -N/2 (position N/2) and,
+// to make the sets disjoint, no earlier axis at -N/2, give the part of
+// f_N(k - x) that is not real:
+//   sum_ax (-1)^{i_ax} c_ax T_ax(other indices),  c_ax = exp(i pi (N/2) x_ax / L),
+// with T_ax the inverse transform over the other axes of that masked slice of
+// ghat times the other axes' phases.  The table stores V_ax = Im(c_ax T_ax).
+// Both kernels read the compact masked slices written by the forward pass.
+// 3D: block (axis, block of field pairs).  Two fields per transform: with D_x
+// the masked Nyquist slice times field x's phases (and c_ax),
+// Im(IDFT(D_x)) = IDFT((D_x(j) - conj D_x(-j)) / (2i)), whose input is
+// Hermitian, so IDFT(Dh_a + i Dh_b) = V_a + i V_b.
+template <typename T, int N>
+__global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
+k_nyquist_3d(const cx<T> *__restrict__ phase, T *__restrict__ V, const cx<T> *__restrict__ tw_g,
+             const cx<T> *__restrict__ nslice, int field0, int nfields, int pairs_per_block) {
+    typedef LineCfg<T, N> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *work = tw + N;
+    cx<T> *scratch = work + N * WP;
+    load_twiddles<T, N>(tw, tw_g);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = lane % LPW, t = lane / LPW;
+    const int row = warp * LPW + c;           // index along b0
+    const int z = threadIdx.x % N, ty = threadIdx.x / N;
+    cx<T> *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
+    const size_t NN = (size_t)N * N;
+    const int npairs = (nfields + 1) / 2;
+    const int ubeg = blockIdx.y * pairs_per_block;
+    const int uend = min(npairs, ubeg + pairs_per_block);
+    constexpr int H2 = N / 2;
+    const int ax = blockIdx.x;
+    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+    const int mrow = (N - row) & (N - 1);
+    const cx<T> *S = nslice + (size_t)ax * NN;
+    for (int y = ubeg; y < uend; ++y) {
+        const int fa = 2 * y, fb = 2 * y + 1 < nfields ? 2 * y + 1 : -1;
+        cx<T> v[E];
+        const cx<T> *pa = phase + (size_t)(field0 + fa) * 3 * N;
+        const cx<T> ca = pa[ax * N + H2];
+        const cx<T> ra = cmul<T>(ca, pa[b0 * N + row]), rma = cmul<T>(ca, pa[b0 * N + mrow]);
+        const cx<T> *pb = fb >= 0 ? phase + (size_t)(field0 + fb) * 3 * N : pa;
+        const cx<T> cb = pb[ax * N + H2];
+        const cx<T> rb = cmul<T>(cb, pb[b0 * N + row]), rmb = cmul<T>(cb, pb[b0 * N + mrow]);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int col = t + e * TPL, mcol = (N - col) & (N - 1);
+            const cx<T> s0 = S[(size_t)row * N + col], s1 = S[(size_t)mrow * N + mcol];
+            // (D(j) - conj D(-j)) / (2i) for each field
+            const cx<T> da = cmul<T>(s0, cmul<T>(ra, pa[b1 * N + col]));
+            const cx<T> dma = cmul<T>(s1, cmul<T>(rma, pa[b1 * N + mcol]));
+            const cx<T> wa = mkc<T>(da.x - dma.x, da.y + dma.y);
+            const cx<T> ha = mkc<T>((T)0.5 * wa.y, (T)-0.5 * wa.x);
+            cx<T> hb = mkc<T>((T)0, (T)0);
+            if (fb >= 0) {
+                const cx<T> db = cmul<T>(s0, cmul<T>(rb, pb[b1 * N + col]));
+                const cx<T> dmb = cmul<T>(s1, cmul<T>(rmb, pb[b1 * N + mcol]));
+                const cx<T> wb = mkc<T>(db.x - dmb.x, db.y + dmb.y);
+                hb = mkc<T>((T)0.5 * wb.y, (T)-0.5 * wb.x);
+            }
+            v[e] = mkc<T>(ha.x - hb.y, ha.y + hb.x);
+        }
+        line_fft<T, N, E, +1>(v, t, rscr, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
+        col_fft<T, N, E, +1>(v, ty, scratch, z, N, tw);
+        T *outa = V + ((size_t)fa * 3 + ax) * NN;
+#pragma unroll
+        for (int e = 0; e < E; ++e) outa[(ty + e * TPL) * N + z] = v[e].x;
+        if (fb >= 0) {
+            T *outb = V + ((size_t)fb * 3 + ax) * NN;
+#pragma unroll
+            for (int e = 0; e < E; ++e) outb[(ty + e * TPL) * N + z] = v[e].y;
+        }
+        __syncthreads();
+    }
+}
+
+// 2D: item = (field of the chunk, axis); the slice is a line along the other
+// axis.  One warp per block holds LPW items (one line each).
+template <typename T, int N>
+__global__ void __launch_bounds__(32)
+k_nyquist_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, T *__restrict__ V,
+             const cx<T> *__restrict__ tw_g, int field0, int nitems) {
+    typedef LineCfg<T, N> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, H2 = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *scratch = tw + N;
+    load_twiddles<T, N>(tw, tw_g);
+    const int lane = threadIdx.x & 31;
+    const int c = lane % LPW, t = lane / LPW;
+    const int item = blockIdx.x * LPW + c;
+    const bool valid = item < nitems;
+    const int it = valid ? item : nitems - 1;
+    const int fl = it >> 1, ax = it & 1;
+    const int b = 1 - ax;
+    const cx<T> *ph = phase + (size_t)(field0 + fl) * 2 * N;
+    cx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int jb = t + e * TPL;
+        const size_t idx = ax == 0 ? (size_t)H2 * N + jb : (size_t)jb * N + H2;
+        const bool masked = ax == 1 && jb == H2;
+        v[e] = masked ? mkc<T>(0, 0) : cmul<T>(ghat[idx], ph[b * N + jb]);
+    }
+    line_fft<T, N, E, +1>(v, t, scratch + (size_t)c * LinePad<N>::PITCH, tw);
+    if (valid) {
+        const cx<T> cax = ph[ax * N + H2];
+        T *out = V + ((size_t)fl * 2 + ax) * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) out[t + e * TPL] = cax.x * v[e].y + cax.y * v[e].x;
+    }
 }
 
 // ------------------------------------------------------------------ pass 2
@@ -234,61 +425,140 @@ template <typename T, int N> struct Pass2Cfg {
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? (E == 4 ? 3 : 2) : (E == 4 ? 2 : 1);
 };
 
-template <typename T, int N, bool IM>
+// Asynchronous global -> shared copy of one complex value (cp.async); the
+// issuing thread later reads the same slot after cp.async.wait_group.
+template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T> *dst, const cx<T> *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Imaginary part of the Nyquist contribution of one field at point (i1,
+// column): sum_ax (-1)^{i_ax} V_ax(other indices).  `Vf` holds the field's d
+// tables; the column is (i2, i3) in 3D, i2 in 2D.
+template <typename T, int N>
+__device__ __forceinline__ T nyq_imag(const T *__restrict__ Vf, int d, int i1, int col) {
+    if (d == 3) {
+        const int i2 = col / N, i3 = col - i2 * N;
+        const T v0 = Vf[col];
+        const T v1 = Vf[N * N + i1 * N + i3];
+        const T v2 = Vf[2 * N * N + i1 * N + i2];
+        return ((i1 & 1) ? -v0 : v0) + ((i2 & 1) ? -v1 : v1) + ((i3 & 1) ? -v2 : v2);
+    }
+    const T v0 = Vf[col];
+    const T v1 = Vf[N + i1];
+    return ((i1 & 1) ? -v0 : v0) + ((col & 1) ? -v1 : v1);
+}
+
+// Block (column tile, group of the chunk).  The group's C unit holds C in its
+// real slot (even group of a pair) or imaginary slot (odd group); each
+// product unit holds A (real slot) and B (imaginary slot).  With the unit's
+// axis-0 transform Z and the Nyquist imaginary parts a (of the real-slot
+// field) and b (of the imaginary-slot field):
+//   real-slot field = (Re Z + b) + i a,  imaginary-slot field = (Im Z - a) + i b.
+// Then, keeping s = C + F and cf = C F, each product contributes
+// A B (C + F) - C F (A + B) = B (A s - cf) - cf A.
+template <typename T, int N, bool IM, bool NYQ>
 __global__ void __launch_bounds__(Pass2Cfg<T, N>::THREADS, Pass2Cfg<T, N>::MIN_BLOCKS)
-k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
-        const int *__restrict__ prod_local, const double *__restrict__ prod_W, const cx<T> *__restrict__ tw_g, int P,
-        int CB, int FPG, int PPG, int g0) {
+k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__restrict__ f, double *__restrict__ Qacc,
+        double *__restrict__ Qim, const int *__restrict__ prod_local, const double *__restrict__ prod_W,
+        const cx<T> *__restrict__ tw_g, int d, int P, int CB, int FPG, int PPG, int g0, int ng) {
     typedef Pass2Cfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
+    cx<T> *stage = scratch + LinePad<N>::LEN * CB;   // 2 tiles of N x CB, prefetched
     load_twiddles<T, N>(tw, tw_g);
     const int z = threadIdx.x % CB, t = threadIdx.x / CB;
     const int col = blockIdx.x * CB + z;
     const int gl = blockIdx.y;
     const size_t ND = (size_t)N * P;
-    const cx<T> *Hg = H + (size_t)gl * FPG * ND;
-
-    cx<T> v[E], s[E], cf[E];
+    const size_t VS = (size_t)d * (ND / N);   // Nyquist table floats per field
+    const int ncu = (ng + 1) >> 1;
+    const cx<T> *Hc = H + (size_t)(gl >> 1) * ND;                       // this group's C unit
+    const cx<T> *Hp = H + (size_t)(ncu + gl * PPG) * ND;               // its product units
+    const int tiles = 1 + PPG;
+    auto prefetch = [&](int k) {
+        const cx<T> *src = k == 0 ? Hc : Hp + (size_t)(k - 1) * ND;
+        cx<T> *dst = stage + (k & 1) * N * CB;
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = Hg[(size_t)(t + e * TPL) * P + col];
-    col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
+        for (int e = 0; e < E; ++e)
+            cp_async_cx<T>(dst + (t + e * TPL) * CB + z, src + (size_t)(t + e * TPL) * P + col);
+        cp_async_commit();
+    };
+    auto take = [&](int k, cx<T> (&v)[E]) {
+        const cx<T> *src = stage + (k & 1) * N * CB;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = src[(t + e * TPL) * CB + z];
+    };
+
+    prefetch(0);
+    if (tiles > 1) prefetch(1);
+    else cp_async_commit();
+    cx<T> v[E], s[E], cf[E];
+    cp_async_wait<1>();
+    take(0, v);
+    col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);   // its barriers also order the stage reads
+    {
+        const bool odd = gl & 1;
+        const int partner = gl ^ 1;
+        const T *Vself = Vtab + (size_t)(gl * FPG) * VS;
+        const T *Vpart = Vtab + (size_t)(partner * FPG) * VS;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i1 = t + e * TPL;
+            T cr = odd ? v[e].y : v[e].x, ci = (T)0;
+            if (NYQ) {
+                const T a_self = nyq_imag<T, N>(Vself, d, i1, col);
+                const T a_part = partner < ng ? nyq_imag<T, N>(Vpart, d, i1, col) : (T)0;
+                cr += odd ? -a_part : a_part;
+                ci = a_self;
+            }
+            const T F = f[(size_t)i1 * P + col];
+            s[e] = mkc<T>(cr + F, ci);
+            cf[e] = mkc<T>(cr * F, ci * F);
+        }
+    }
     T ar[E], ai[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const T F = f[(size_t)(t + e * TPL) * P + col];
-        s[e] = mkc<T>(v[e].x + F, v[e].y);
-        cf[e] = mkc<T>(v[e].x * F, v[e].y * F);
         ar[e] = (T)0;
         ai[e] = (T)0;
     }
     const double *Wg = prod_W + (size_t)(g0 + gl) * PPG;
     for (int p = 0; p < PPG; ++p) {
-        const cx<T> *HA = Hg + (size_t)prod_local[2 * p] * ND;
-        const cx<T> *HB = Hg + (size_t)prod_local[2 * p + 1] * ND;
         const T W = (T)Wg[p];
-        cx<T> X[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = HA[(size_t)(t + e * TPL) * P + col];
+        if (p + 2 < tiles) prefetch(p + 2);   // buffer of tile p, already read
+        else cp_async_commit();               // empty group keeps the count uniform
+        cp_async_wait<1>();
+        take(p + 1, v);
         col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
+        const T *Va = Vtab + (size_t)(gl * FPG + prod_local[2 * p]) * VS;
+        const T *Vb = Vtab + (size_t)(gl * FPG + prod_local[2 * p + 1]) * VS;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            X[e] = csub<T>(cmul<T>(v[e], s[e]), cf[e]);
-            const cx<T> q = cmul<T>(cf[e], v[e]);            // added with a minus sign
-            ar[e] -= W * q.x;
-            if (IM) ai[e] -= W * q.y;
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = HB[(size_t)(t + e * TPL) * P + col];
-        col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            ar[e] += W * (v[e].x * X[e].x - v[e].y * X[e].y);
-            if (IM) ai[e] += W * (v[e].x * X[e].y + v[e].y * X[e].x);
+            const int i1 = t + e * TPL;
+            T a = (T)0, b = (T)0;
+            if (NYQ) {
+                a = nyq_imag<T, N>(Va, d, i1, col);
+                b = nyq_imag<T, N>(Vb, d, i1, col);
+            }
+            const cx<T> A = mkc<T>(v[e].x + b, a);
+            const cx<T> B = mkc<T>(v[e].y - a, b);
+            const cx<T> X = csub<T>(cmul<T>(A, s[e]), cf[e]);
+            const cx<T> q = cmul<T>(cf[e], A);             // added with a minus sign
+            ar[e] += W * (B.x * X.x - B.y * X.y - q.x);
+            if (IM) ai[e] += W * (B.x * X.y + B.y * X.x - q.y);
         }
     }
+    cp_async_wait<0>();
     double *Qg = Qacc + (size_t)gl * ND;
 #pragma unroll
     for (int e = 0; e < E; ++e) Qg[(size_t)(t + e * TPL) * P + col] += (double)ar[e];

@@ -54,7 +54,8 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
     if ((rc = set_smem(k_fwd_cols<T, N>, smem))) return rc;
     const double inv_nd = 1.0 / (double)nd_of(hp);
     k_fwd_cols<T, N><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(
-        tmp, static_cast<cx<T> *>(p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO);
+        tmp, static_cast<cx<T> *>(p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO,
+        hp.nyquist == WKE_NYQ_KEEP ? static_cast<cx<T> *>(p.nslice) : nullptr);
     return (int)cudaGetLastError();
 }
 
@@ -62,8 +63,7 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
 template <typename T, int N>
 static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
     typedef LineCfg<T, N> Cfg;
-    const int nfields = ng * hp.fields_per_group;
-    const int field0 = g0 * hp.fields_per_group;
+    const int nunits = chunk_units(hp, ng);
     const cx<T> *ghat = static_cast<const cx<T> *>(p.ghat);
     const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
     cx<T> *H = static_cast<cx<T> *>(p.H);
@@ -74,9 +74,10 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
             const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
             if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
             // enough blocks to fill the GPU several times over
-            const int fpb = std::max(1, std::min(nfields, nfields * N / 1200));
-            dim3 grid(N, (nfields + fpb - 1) / fpb);
-            k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, field0, nfields, fpb);
+            const int upb = std::max(1, std::min(nunits, nunits * N / 1200));
+            dim3 grid(N, (nunits + upb - 1) / upb);
+            k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng,
+                                                               hp.fields_per_group, hp.products_per_group, nunits, upb);
         } else {
             return (int)cudaErrorInvalidValue;
         }
@@ -84,31 +85,65 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
         const int warps = line_warps<T, N>(N);
         const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
         if ((rc = set_smem(k_pass1_2d<T, N>, smem))) return rc;
-        dim3 grid(N / (warps * Cfg::LPW), nfields);
-        k_pass1_2d<T, N><<<grid, warps * 32, smem, s>>>(ghat, ph, H, tw, field0);
+        dim3 grid(N / (warps * Cfg::LPW), nunits);
+        k_pass1_2d<T, N><<<grid, warps * 32, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng, hp.fields_per_group,
+                                                        hp.products_per_group);
+    }
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Nyquist tables
+template <typename T, int N>
+static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+    typedef LineCfg<T, N> Cfg;
+    const int nfields = ng * hp.fields_per_group;
+    const int field0 = g0 * hp.fields_per_group;
+    const cx<T> *ghat = static_cast<const cx<T> *>(p.ghat);
+    const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
+    T *V = static_cast<T *>(p.V);
+    const cx<T> *tw = static_cast<const cx<T> *>(p.tw);
+    int rc = 0;
+    if (hp.d == 3) {
+        if constexpr (N <= 64) {
+            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
+            if ((rc = set_smem(k_nyquist_3d<T, N>, smem))) return rc;
+            const int npairs = (nfields + 1) / 2;
+            k_nyquist_3d<T, N><<<dim3(3, npairs), N * Cfg::TPL, smem, s>>>(
+                ph, V, tw, static_cast<const cx<T> *>(p.nslice), field0, nfields, 1);
+        } else {
+            return (int)cudaErrorInvalidValue;
+        }
+    } else {
+        const int items = 2 * nfields;
+        const size_t smem = (size_t)(N + Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
+        if ((rc = set_smem(k_nyquist_2d<T, N>, smem))) return rc;
+        k_nyquist_2d<T, N><<<(items + Cfg::LPW - 1) / Cfg::LPW, 32, smem, s>>>(ghat, ph, V, tw, field0, items);
     }
     return (int)cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ pass 2
-template <typename T, int N, bool IM>
+template <typename T, int N, bool IM, bool NYQ>
 static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
     typedef Pass2Cfg<T, N> Cfg;
     const int P = cols_of(hp);
     const int CB = std::min(Cfg::CB, P);       // columns per block
-    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB) * sizeof(cx<T>);
+    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB + 2 * N * CB) * sizeof(cx<T>);
     int rc = 0;
-    if ((rc = set_smem(k_pass2<T, N, IM>, smem))) return rc;
+    if ((rc = set_smem(k_pass2<T, N, IM, NYQ>, smem))) return rc;
     dim3 grid(P / CB, ng);
-    k_pass2<T, N, IM><<<grid, CB * Cfg::TPL, smem, s>>>(
-        static_cast<const cx<T> *>(p.H), static_cast<const T *>(p.f), p.Qacc, p.Qacc_im, p.prod_local, p.prod_W,
-        static_cast<const cx<T> *>(p.tw), P, CB, hp.fields_per_group, hp.products_per_group, g0);
+    k_pass2<T, N, IM, NYQ><<<grid, CB * Cfg::TPL, smem, s>>>(
+        static_cast<const cx<T> *>(p.H), static_cast<const T *>(p.V), static_cast<const T *>(p.f), p.Qacc,
+        p.Qacc_im, p.prod_local, p.prod_W, static_cast<const cx<T> *>(p.tw), hp.d, P, CB, hp.fields_per_group,
+        hp.products_per_group, g0, ng);
     return (int)cudaGetLastError();
 }
 
 template <typename T, int N>
 static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
-    return im ? pass2_nim<T, N, true>(hp, p, g0, ng, s) : pass2_nim<T, N, false>(hp, p, g0, ng, s);
+    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
+    if (nyq) return im ? pass2_nim<T, N, true, true>(hp, p, g0, ng, s) : pass2_nim<T, N, false, true>(hp, p, g0, ng, s);
+    return im ? pass2_nim<T, N, true, false>(hp, p, g0, ng, s) : pass2_nim<T, N, false, false>(hp, p, g0, ng, s);
 }
 
 // ------------------------------------------------------------------ dispatch on N
@@ -130,6 +165,17 @@ template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int g
         case 64: return pass1_n<T, 64>(hp, p, g0, ng, s);
         case 128: return pass1_n<T, 128>(hp, p, g0, ng, s);
         case 256: return pass1_n<T, 256>(hp, p, g0, ng, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return nyquist_n<T, 16>(hp, p, g0, ng, s);
+        case 32: return nyquist_n<T, 32>(hp, p, g0, ng, s);
+        case 64: return nyquist_n<T, 64>(hp, p, g0, ng, s);
+        case 128: return nyquist_n<T, 128>(hp, p, g0, ng, s);
+        case 256: return nyquist_n<T, 256>(hp, p, g0, ng, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -185,6 +231,7 @@ template <typename T> int rk_final_T(const HostPlan &hp, void *f, const double *
 #define WKE_INSTANTIATE(T)                                                                                   \
     template int forward_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                         \
     template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);                 \
+    template int nyquist_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);               \
     template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);           \
     template int finalize_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);        \
     template int moments_T<T>(const HostPlan &, const void *, double *, double *, cudaStream_t);           \

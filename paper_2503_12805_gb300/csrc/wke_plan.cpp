@@ -322,9 +322,10 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
     size_t nd = 1;
     for (int a = 0; a < d; ++a) nd *= (size_t)N;
-    size_t per_group = (size_t)hp.fields_per_group * nd * cxb;
+    // two groups share one C unit, so a group costs products + 1/2 units
+    size_t per_pair = (size_t)(2 * hp.products_per_group + 1) * nd * cxb;
     hp.chunk_bytes = quad->chunk_bytes ? quad->chunk_bytes : (size_t)48 << 20;
-    hp.groups_per_chunk = (int)std::max<size_t>(1, hp.chunk_bytes / per_group);
+    hp.groups_per_chunk = (int)std::max<size_t>(1, 2 * (hp.chunk_bytes / per_pair));
     hp.groups_per_chunk = std::min(hp.groups_per_chunk, hp.n_groups);
     hp.n_chunks = (hp.n_groups + hp.groups_per_chunk - 1) / hp.groups_per_chunk;
 
@@ -341,6 +342,18 @@ void phase_row(int N, double L, double x, double *out) {
     }
 }
 
+static size_t grid_size(const HostPlan &hp);
+
+size_t chunk_unit_bytes(const HostPlan &hp) {
+    size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
+    return std::max((size_t)chunk_units(hp, hp.groups_per_chunk) * grid_size(hp) * cxb, grid_size(hp) * 16);
+}
+
+size_t chunk_v_bytes(const HostPlan &hp) {
+    size_t tb = hp.precision == WKE_FP64 ? 8 : 4;
+    return (size_t)hp.groups_per_chunk * hp.fields_per_group * hp.d * (grid_size(hp) / hp.N) * tb;
+}
+
 static size_t grid_size(const HostPlan &hp) {
     size_t nd = 1;
     for (int a = 0; a < hp.d; ++a) nd *= (size_t)hp.N;
@@ -353,8 +366,8 @@ size_t plan_device_bytes(const HostPlan &hp) {
     size_t cxb = 2 * tb;
     size_t n_fields = (size_t)hp.n_groups * hp.fields_per_group;
     size_t bytes = 0;
-    bytes += nd * cxb;                                                  // ghat
-    bytes += 2 * std::max((size_t)hp.groups_per_chunk * hp.fields_per_group * nd * cxb, nd * 16);  // H x 2
+    bytes += nd * cxb + hp.d * (nd / hp.N) * cxb;                       // ghat, Nyquist slices
+    bytes += 2 * chunk_unit_bytes(hp) + 2 * chunk_v_bytes(hp);          // H, V double-buffered
     bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
     bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
@@ -366,23 +379,36 @@ size_t plan_device_bytes(const HostPlan &hp) {
     return bytes;
 }
 
+// Units transformed per evaluation (C units of every chunk + product units).
+static double total_units(const HostPlan &hp) {
+    double u = 0;
+    for (int c = 0; c < hp.n_chunks; ++c) {
+        int ng = std::min(hp.groups_per_chunk, hp.n_groups - c * hp.groups_per_chunk);
+        u += chunk_units(hp, ng);
+    }
+    return u;
+}
+
 double plan_flops(const HostPlan &hp) {
     double nd = (double)grid_size(hp);
     double lg = std::log2(nd);
+    double units = total_units(hp);
     double n_fields = (double)hp.n_groups * hp.fields_per_group;
     double n_prod = (double)hp.n_groups * hp.products_per_group;
     double fwd = 5.0 * nd * lg;
-    double inv = n_fields * 5.0 * nd * lg;
-    double phases = n_fields * nd * 12.0;      // two complex products per point
-    double prods = n_prod * nd * 30.0;         // cubic product, weight, accumulate
-    return fwd + inv + phases + prods;
+    double inv = units * 5.0 * nd * lg;                    // pass 1 + pass 2 transforms
+    double c_units = units - (double)hp.n_groups * hp.products_per_group;
+    double c_again = ((double)hp.n_groups - c_units) * 5.0 * nd * std::log2((double)hp.N);  // shared C units, axis 0
+    double nyq = hp.nyquist == WKE_NYQ_KEEP ? n_fields * hp.d * 5.0 * (nd / hp.N) * std::log2(nd / hp.N) : 0.0;
+    double phases = units * nd * 16.0;                     // two phase products and the packing per point
+    double prods = n_prod * nd * 30.0;                     // cubic product, weight, accumulate
+    return fwd + inv + c_again + nyq + phases + prods;
 }
 
 double plan_l2_bytes(const HostPlan &hp) {
     double nd = (double)grid_size(hp);
     double cxb = hp.precision == WKE_FP64 ? 16.0 : 8.0;
-    double n_fields = (double)hp.n_groups * hp.fields_per_group;
-    return n_fields * nd * cxb * 2.0;          // each intermediate written once, read once
+    return total_units(hp) * nd * cxb * 2.0;  // each unit written once, read (about) once
 }
 
 }  // namespace wke

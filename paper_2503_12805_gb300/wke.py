@@ -65,7 +65,7 @@ EXPORTED = [
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_moments_noalloc", "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
 ]
-PROF_CLASSES = ("forward", "pass1", "pass2", "finalize")
+PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
