@@ -296,8 +296,8 @@ def kernel_flops(cls, info):
     if cls == "pass2":
         per_group = (1 + ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
         return G * per_group
-    if cls == "nyquist":
-        return G * info.fields_per_group * d * 5.0 * P * math.log2(P)
+    if cls == "nyquist":   # a chunk's units, two fields per transform
+        return units * d * 5.0 * P * math.log2(P)
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * G * nd

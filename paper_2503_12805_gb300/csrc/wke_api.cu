@@ -46,9 +46,11 @@ struct wke_plan {
     DevicePtrs dp{};
     void *Hbuf[2] = {nullptr, nullptr};   // double-buffered chunk intermediates
     void *Vbuf[2] = {nullptr, nullptr};   // double-buffered chunk Nyquist tables
-    // pass 1 of chunk c+1 runs on s1 while pass 2 of chunk c runs on s2
-    cudaStream_t s1 = nullptr, s2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
+    // pass 1 of chunk c+1 runs on s1 while pass 2 of chunk c runs on s2; the
+    // Nyquist tables of each chunk are built on s3
+    cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fwd = nullptr;
+    cudaEvent_t ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr}, ev_nq[2] = {nullptr, nullptr};
     bool use_graphs = true;
     std::vector<GraphEntry> graphs;
     unsigned long long tick = 0;
@@ -95,11 +97,12 @@ void free_graphs(wke_plan *p) {
 
 void free_plan(wke_plan *p) {
     free_graphs(p);
-    for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_p1[0], p->ev_p1[1], p->ev_p2[0], p->ev_p2[1]})
+    for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_fwd, p->ev_p1[0], p->ev_p1[1], p->ev_p2[0], p->ev_p2[1],
+                          p->ev_nq[0], p->ev_nq[1]})
         if (e) cudaEventDestroy(e);
-    if (p->s1) cudaStreamDestroy(p->s1);
-    if (p->s2) cudaStreamDestroy(p->s2);
-    p->s1 = p->s2 = nullptr;
+    for (cudaStream_t st : {p->s1, p->s2, p->s3})
+        if (st) cudaStreamDestroy(st);
+    p->s1 = p->s2 = p->s3 = nullptr;
     for (void *ptr : p->allocs) cudaFree(ptr);
     p->allocs.clear();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -211,7 +214,8 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
     dp.fwd_tmp = p->Hbuf[0];
     // while profiling, both passes share one stream so that each launch's
     // interval measures that kernel alone
-    cudaStream_t s1 = p->s1, s2 = p->profiling ? p->s1 : p->s2;
+    cudaStream_t s1 = p->s1, s2 = p->profiling ? p->s1 : p->s2, s3 = p->profiling ? p->s1 : p->s3;
+    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
     int e = (int)cudaEventRecord(p->ev_fork, origin);
     if (!e) e = (int)cudaStreamWaitEvent(s1, p->ev_fork, 0);
     if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_fork, 0);
@@ -219,23 +223,32 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         ProfScope ps(p, s1, 0);
         e = forward_T<T>(hp, dp, s1);
     }
+    // s3 joins only when it has work (a forked stream must be joined back)
+    if (nyq && !e) e = (int)cudaEventRecord(p->ev_fwd, s1);
+    if (nyq && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_fwd, 0);
     for (int c = 0; c < hp.n_chunks && !e; ++c) {
         const int g0 = c * hp.groups_per_chunk;
         const int ng = std::min(hp.groups_per_chunk, hp.n_groups - g0);
         const int buf = c & 1;
         dp.H = p->Hbuf[buf];
         dp.V = p->Vbuf[buf];
-        if (c >= 2) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
-        if (!e && hp.nyquist == WKE_NYQ_KEEP) {
-            ProfScope ps(p, s1, 4);
-            e = nyquist_T<T>(hp, dp, g0, ng, s1);
+        if (nyq) {
+            // tables of chunk c on s3, once pass 2 of chunk c-2 has read the buffer
+            if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_p2[buf], 0);
+            if (!e) {
+                ProfScope ps(p, s3, 4);
+                e = nyquist_T<T>(hp, dp, c, 1, s3);
+            }
+            if (!e) e = (int)cudaEventRecord(p->ev_nq[buf], s3);
         }
+        if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
         if (!e) {
             ProfScope ps(p, s1, 1);
             e = pass1_T<T>(hp, dp, g0, ng, s1);
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p1[buf], s1);
         if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_p1[buf], 0);
+        if (!e && nyq) e = (int)cudaStreamWaitEvent(s2, p->ev_nq[buf], 0);
         if (!e) {
             ProfScope ps(p, s2, 2);
             e = pass2_T<T>(hp, dp, g0, ng, Qim != nullptr, s2);
@@ -364,8 +377,10 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
     ALLOC(p->dp.nslice, (size_t)hp.d * (nd / hp.N) * cxb);
     ALLOC(p->Hbuf[0], chunk_unit_bytes(hp));
     ALLOC(p->Hbuf[1], chunk_unit_bytes(hp));
-    ALLOC(p->Vbuf[0], chunk_v_bytes(hp));
-    ALLOC(p->Vbuf[1], chunk_v_bytes(hp));
+    if (hp.nyquist == WKE_NYQ_KEEP) {
+        ALLOC(p->Vbuf[0], chunk_v_bytes(hp));
+        ALLOC(p->Vbuf[1], chunk_v_bytes(hp));
+    }
     p->dp.H = p->dp.fwd_tmp = p->Hbuf[0];
     ALLOC(p->dp.Qacc, (size_t)hp.groups_per_chunk * nd * 8);
     ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
@@ -386,7 +401,9 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
     {
         cudaError_t e = cudaStreamCreateWithFlags(&p->s1, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking);
-        for (cudaEvent_t *ev : {&p->ev_fork, &p->ev_join, &p->ev_p1[0], &p->ev_p1[1], &p->ev_p2[0], &p->ev_p2[1]})
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s3, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&p->ev_fork, &p->ev_join, &p->ev_fwd, &p->ev_p1[0], &p->ev_p1[1], &p->ev_p2[0],
+                                &p->ev_p2[1], &p->ev_nq[0], &p->ev_nq[1]})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "stream and event creation");

@@ -76,7 +76,7 @@ struct DevicePtrs {
     void *ghat;               // N^d complex T: coefficients of f (DFT order)
     void *fwd_tmp;            // N^d complex double: forward-transform scratch
     void *H;                  // chunk intermediate units, complex T
-    void *V;                  // chunk Nyquist tables, real T: per field, d tables of N^{d-1}
+    void *V;                  // chunk Nyquist tables: per unit, d tables of N^{d-1} (V_a, V_b) pairs
     void *nslice;             // d masked Nyquist slices of ghat, N^{d-1} complex T each
     double *Qacc;             // groups_per_chunk * N^d partial sums (real)
     double *Qacc_im;          // groups_per_chunk * N^d partial sums (imag) or null

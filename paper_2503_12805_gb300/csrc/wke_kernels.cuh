@@ -294,16 +294,27 @@ __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restri
 // with T_ax the inverse transform over the other axes of that masked slice of
 // ghat times the other axes' phases.  The table stores V_ax = Im(c_ax T_ax).
 // Both kernels read the compact masked slices written by the forward pass.
-// 3D: block (axis, block of field pairs).  Two fields per transform: with D_x
-// the masked Nyquist slice times field x's phases (and c_ax),
-// Im(IDFT(D_x)) = IDFT((D_x(j) - conj D_x(-j)) / (2i)), whose input is
-// Hermitian, so IDFT(Dh_a + i Dh_b) = V_a + i V_b.
+// 3D: block (axis, block of units).  The two fields of a unit share one
+// transform: with D_x the masked Nyquist slice times field x's phases (and
+// c_ax), Im(IDFT(D_x)) = IDFT((D_x(j) - conj D_x(-j)) / (2i)), whose input is
+// Hermitian, so IDFT(Dh_a + i Dh_b) = V_a + i V_b.  The unit's tables are
+// stored interleaved (V_a, V_b), the layout pass 2 reads.
+template <typename T>
+__device__ __forceinline__ cx<T> herm_half(cx<T> d, cx<T> dm) {
+    // (d - conj(dm)) / (2i)
+    return mkc<T>((T)0.5 * (d.y + dm.y), (T)-0.5 * (d.x - dm.x));
+}
+
+// Grid (axis, unit of the chunk, chunk - chunk0): chunk c covers groups
+// [c G, min((c + 1) G, n_groups)) and its units start at
+// V + (c - chunk0) * units_per_chunk * 3 * N^2.
 template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
-k_nyquist_3d(const cx<T> *__restrict__ phase, T *__restrict__ V, const cx<T> *__restrict__ tw_g,
-             const cx<T> *__restrict__ nslice, int field0, int nfields, int pairs_per_block) {
+k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T> *__restrict__ tw_g,
+             const cx<T> *__restrict__ nslice, const int *__restrict__ prod_local, int G, int n_groups, int FPG,
+             int PPG, int units_per_chunk, int chunk0) {
     typedef LineCfg<T, N> Cfg;
-    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH, H2 = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *work = tw + N;
@@ -315,66 +326,52 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, T *__restrict__ V, const cx<T> *__
     const int z = threadIdx.x % N, ty = threadIdx.x / N;
     cx<T> *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
     const size_t NN = (size_t)N * N;
-    const int npairs = (nfields + 1) / 2;
-    const int ubeg = blockIdx.y * pairs_per_block;
-    const int uend = min(npairs, ubeg + pairs_per_block);
-    constexpr int H2 = N / 2;
-    const int ax = blockIdx.x;
+    const int ax = blockIdx.x, u = blockIdx.y;
+    const int g0 = (chunk0 + blockIdx.z) * G, ng = min(G, n_groups - g0);
+    if (u >= (ng + 1) / 2 + ng * PPG) return;   // block-uniform
+    V += (size_t)blockIdx.z * units_per_chunk * 3 * NN;
     const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
     const int mrow = (N - row) & (N - 1);
     const cx<T> *S = nslice + (size_t)ax * NN;
-    for (int y = ubeg; y < uend; ++y) {
-        const int fa = 2 * y, fb = 2 * y + 1 < nfields ? 2 * y + 1 : -1;
-        cx<T> v[E];
-        const cx<T> *pa = phase + (size_t)(field0 + fa) * 3 * N;
-        const cx<T> ca = pa[ax * N + H2];
-        const cx<T> ra = cmul<T>(ca, pa[b0 * N + row]), rma = cmul<T>(ca, pa[b0 * N + mrow]);
-        const cx<T> *pb = fb >= 0 ? phase + (size_t)(field0 + fb) * 3 * N : pa;
-        const cx<T> cb = pb[ax * N + H2];
-        const cx<T> rb = cmul<T>(cb, pb[b0 * N + row]), rmb = cmul<T>(cb, pb[b0 * N + mrow]);
+    int fa, fb;
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    const cx<T> *pa = phase + (size_t)fa * 3 * N;
+    const cx<T> ca = pa[ax * N + H2];
+    const cx<T> ra = cmul<T>(ca, pa[b0 * N + row]), rma = cmul<T>(ca, pa[b0 * N + mrow]);
+    const cx<T> *pb = fb >= 0 ? phase + (size_t)fb * 3 * N : pa;
+    const cx<T> cb = pb[ax * N + H2];
+    const cx<T> rb = cmul<T>(cb, pb[b0 * N + row]), rmb = cmul<T>(cb, pb[b0 * N + mrow]);
+    cx<T> v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int col = t + e * TPL, mcol = (N - col) & (N - 1);
-            const cx<T> s0 = S[(size_t)row * N + col], s1 = S[(size_t)mrow * N + mcol];
-            // (D(j) - conj D(-j)) / (2i) for each field
-            const cx<T> da = cmul<T>(s0, cmul<T>(ra, pa[b1 * N + col]));
-            const cx<T> dma = cmul<T>(s1, cmul<T>(rma, pa[b1 * N + mcol]));
-            const cx<T> wa = mkc<T>(da.x - dma.x, da.y + dma.y);
-            const cx<T> ha = mkc<T>((T)0.5 * wa.y, (T)-0.5 * wa.x);
-            cx<T> hb = mkc<T>((T)0, (T)0);
-            if (fb >= 0) {
-                const cx<T> db = cmul<T>(s0, cmul<T>(rb, pb[b1 * N + col]));
-                const cx<T> dmb = cmul<T>(s1, cmul<T>(rmb, pb[b1 * N + mcol]));
-                const cx<T> wb = mkc<T>(db.x - dmb.x, db.y + dmb.y);
-                hb = mkc<T>((T)0.5 * wb.y, (T)-0.5 * wb.x);
-            }
-            v[e] = mkc<T>(ha.x - hb.y, ha.y + hb.x);
-        }
-        line_fft<T, N, E, +1>(v, t, rscr, tw);
-#pragma unroll
-        for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
-        col_fft<T, N, E, +1>(v, ty, scratch, z, N, tw);
-        T *outa = V + ((size_t)fa * 3 + ax) * NN;
-#pragma unroll
-        for (int e = 0; e < E; ++e) outa[(ty + e * TPL) * N + z] = v[e].x;
-        if (fb >= 0) {
-            T *outb = V + ((size_t)fb * 3 + ax) * NN;
-#pragma unroll
-            for (int e = 0; e < E; ++e) outb[(ty + e * TPL) * N + z] = v[e].y;
-        }
-        __syncthreads();
+    for (int e = 0; e < E; ++e) {
+        const int col = t + e * TPL, mcol = (N - col) & (N - 1);
+        const cx<T> s0 = S[(size_t)row * N + col], s1 = S[(size_t)mrow * N + mcol];
+        const cx<T> ha = herm_half<T>(cmul<T>(s0, cmul<T>(ra, pa[b1 * N + col])),
+                                      cmul<T>(s1, cmul<T>(rma, pa[b1 * N + mcol])));
+        cx<T> hb = mkc<T>((T)0, (T)0);
+        if (fb >= 0)
+            hb = herm_half<T>(cmul<T>(s0, cmul<T>(rb, pb[b1 * N + col])), cmul<T>(s1, cmul<T>(rmb, pb[b1 * N + mcol])));
+        v[e] = mkc<T>(ha.x - hb.y, ha.y + hb.x);
     }
+    line_fft<T, N, E, +1>(v, t, rscr, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
+    col_fft<T, N, E, +1>(v, ty, scratch, z, N, tw);
+    cx<T> *out = V + ((size_t)u * 3 + ax) * NN;
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
 }
 
-// 2D: item = (field of the chunk, axis); the slice is a line along the other
-// axis.  One warp per block holds LPW items (one line each).
+// 2D: item = (unit, axis); the slice is a line along the other axis.  One
+// warp per block holds LPW items (one line each).
 template <typename T, int N>
 __global__ void __launch_bounds__(32)
-k_nyquist_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, T *__restrict__ V,
-             const cx<T> *__restrict__ tw_g, int field0, int nitems) {
+k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T> *__restrict__ tw_g,
+             const cx<T> *__restrict__ nslice, const int *__restrict__ prod_local, int G, int n_groups, int FPG,
+             int PPG, int units_per_chunk, int chunk0) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, H2 = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -383,26 +380,36 @@ k_nyquist_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, T 
     load_twiddles<T, N>(tw, tw_g);
     const int lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
+    const int g0 = (chunk0 + blockIdx.y) * G, ng = min(G, n_groups - g0);
+    const int nitems = 2 * ((ng + 1) / 2 + ng * PPG);
+    V += (size_t)blockIdx.y * units_per_chunk * 2 * N;
     const int item = blockIdx.x * LPW + c;
     const bool valid = item < nitems;
     const int it = valid ? item : nitems - 1;
-    const int fl = it >> 1, ax = it & 1;
+    const int u = it >> 1, ax = it & 1;
     const int b = 1 - ax;
-    const cx<T> *ph = phase + (size_t)(field0 + fl) * 2 * N;
+    int fa, fb;
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    const cx<T> *pa = phase + (size_t)fa * 2 * N;
+    const cx<T> *pb = fb >= 0 ? phase + (size_t)fb * 2 * N : pa;
+    const cx<T> ca = pa[ax * N + H2], cb = pb[ax * N + H2];
+    const cx<T> *S = nslice + (size_t)ax * N;
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int jb = t + e * TPL;
-        const size_t idx = ax == 0 ? (size_t)H2 * N + jb : (size_t)jb * N + H2;
-        const bool masked = ax == 1 && jb == H2;
-        v[e] = masked ? mkc<T>(0, 0) : cmul<T>(ghat[idx], ph[b * N + jb]);
+        const int jb = t + e * TPL, mj = (N - jb) & (N - 1);
+        const cx<T> s0 = S[jb], s1 = S[mj];
+        const cx<T> ha = herm_half<T>(cmul<T>(s0, cmul<T>(ca, pa[b * N + jb])), cmul<T>(s1, cmul<T>(ca, pa[b * N + mj])));
+        cx<T> hb = mkc<T>((T)0, (T)0);
+        if (fb >= 0)
+            hb = herm_half<T>(cmul<T>(s0, cmul<T>(cb, pb[b * N + jb])), cmul<T>(s1, cmul<T>(cb, pb[b * N + mj])));
+        v[e] = mkc<T>(ha.x - hb.y, ha.y + hb.x);
     }
     line_fft<T, N, E, +1>(v, t, scratch + (size_t)c * LinePad<N>::PITCH, tw);
     if (valid) {
-        const cx<T> cax = ph[ax * N + H2];
-        T *out = V + ((size_t)fl * 2 + ax) * N;
+        cx<T> *out = V + ((size_t)u * 2 + ax) * N;
 #pragma unroll
-        for (int e = 0; e < E; ++e) out[t + e * TPL] = cax.x * v[e].y + cax.y * v[e].x;
+        for (int e = 0; e < E; ++e) out[t + e * TPL] = v[e];
     }
 }
 
@@ -439,21 +446,24 @@ template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
-// Imaginary part of the Nyquist contribution of one field at point (i1,
-// column): sum_ax (-1)^{i_ax} V_ax(other indices).  `Vf` holds the field's d
-// tables; the column is (i2, i3) in 3D, i2 in 2D.
+// Imaginary parts of the Nyquist contributions of a unit's two fields at
+// point (i1, column): sum_ax (-1)^{i_ax} V_ax(other indices), real-slot field
+// in .x and imaginary-slot field in .y.  `Vu` holds the unit's d interleaved
+// tables; the column is (i2, i3) in 3D, i2 in 2D; sgn1 = (-1)^{i1}.
 template <typename T, int N>
-__device__ __forceinline__ T nyq_imag(const T *__restrict__ Vf, int d, int i1, int col) {
+__device__ __forceinline__ cx<T> nyq_pair(const cx<T> *__restrict__ Vu, int d, int i1, int col, T sgn1) {
     if (d == 3) {
         const int i2 = col / N, i3 = col - i2 * N;
-        const T v0 = Vf[col];
-        const T v1 = Vf[N * N + i1 * N + i3];
-        const T v2 = Vf[2 * N * N + i1 * N + i2];
-        return ((i1 & 1) ? -v0 : v0) + ((i2 & 1) ? -v1 : v1) + ((i3 & 1) ? -v2 : v2);
+        const T sg2 = (i2 & 1) ? (T)-1 : (T)1, sg3 = (i3 & 1) ? (T)-1 : (T)1;
+        const cx<T> v0 = Vu[col];
+        const cx<T> v1 = Vu[N * N + i1 * N + i3];
+        const cx<T> v2 = Vu[2 * N * N + i1 * N + i2];
+        return mkc<T>(sgn1 * v0.x + sg2 * v1.x + sg3 * v2.x, sgn1 * v0.y + sg2 * v1.y + sg3 * v2.y);
     }
-    const T v0 = Vf[col];
-    const T v1 = Vf[N + i1];
-    return ((i1 & 1) ? -v0 : v0) + ((col & 1) ? -v1 : v1);
+    const T sg2 = (col & 1) ? (T)-1 : (T)1;
+    const cx<T> v0 = Vu[col];
+    const cx<T> v1 = Vu[N + i1];
+    return mkc<T>(sgn1 * v0.x + sg2 * v1.x, sgn1 * v0.y + sg2 * v1.y);
 }
 
 // Block (column tile, group of the chunk).  The group's C unit holds C in its
@@ -463,12 +473,13 @@ __device__ __forceinline__ T nyq_imag(const T *__restrict__ Vf, int d, int i1, i
 // field) and b (of the imaginary-slot field):
 //   real-slot field = (Re Z + b) + i a,  imaginary-slot field = (Im Z - a) + i b.
 // Then, keeping s = C + F and cf = C F, each product contributes
-// A B (C + F) - C F (A + B) = B (A s - cf) - cf A.
+// A B (C + F) - C F (A + B) = B (A s - cf) - cf A, written out in real parts.
 template <typename T, int N, bool IM, bool NYQ>
 __global__ void __launch_bounds__(Pass2Cfg<T, N>::THREADS, Pass2Cfg<T, N>::MIN_BLOCKS)
-k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__restrict__ f, double *__restrict__ Qacc,
-        double *__restrict__ Qim, const int *__restrict__ prod_local, const double *__restrict__ prod_W,
-        const cx<T> *__restrict__ tw_g, int d, int P, int CB, int FPG, int PPG, int g0, int ng) {
+k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
+        double *__restrict__ Qacc, double *__restrict__ Qim, const int *__restrict__ prod_local,
+        const double *__restrict__ prod_W, const cx<T> *__restrict__ tw_g, int d, int P, int CB, int PPG, int g0,
+        int ng) {
     typedef Pass2Cfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -480,10 +491,11 @@ k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__rest
     const int col = blockIdx.x * CB + z;
     const int gl = blockIdx.y;
     const size_t ND = (size_t)N * P;
-    const size_t VS = (size_t)d * (ND / N);   // Nyquist table floats per field
+    const size_t VS = (size_t)d * (ND / N);   // Nyquist table entries per unit
     const int ncu = (ng + 1) >> 1;
     const cx<T> *Hc = H + (size_t)(gl >> 1) * ND;                       // this group's C unit
     const cx<T> *Hp = H + (size_t)(ncu + gl * PPG) * ND;               // its product units
+    const T sgn1 = (t & 1) ? (T)-1 : (T)1;    // (-1)^{i1}: TPL is even, so i1 = t + e TPL has t's parity
     const int tiles = 1 + PPG;
     auto prefetch = [&](int k) {
         const cx<T> *src = k == 0 ? Hc : Hp + (size_t)(k - 1) * ND;
@@ -502,28 +514,30 @@ k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__rest
     prefetch(0);
     if (tiles > 1) prefetch(1);
     else cp_async_commit();
-    cx<T> v[E], s[E], cf[E];
+    cx<T> v[E];
+    T sr[E], si[E], cr[E], ci[E];
     cp_async_wait<1>();
     take(0, v);
     col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);   // its barriers also order the stage reads
     {
         const bool odd = gl & 1;
-        const int partner = gl ^ 1;
-        const T *Vself = Vtab + (size_t)(gl * FPG) * VS;
-        const T *Vpart = Vtab + (size_t)(partner * FPG) * VS;
+        const bool has_partner = (gl ^ 1) < ng;
+        const cx<T> *Vc = Vtab + (size_t)(gl >> 1) * VS;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i1 = t + e * TPL;
-            T cr = odd ? v[e].y : v[e].x, ci = (T)0;
+            T re = odd ? v[e].y : v[e].x, im = (T)0;
             if (NYQ) {
-                const T a_self = nyq_imag<T, N>(Vself, d, i1, col);
-                const T a_part = partner < ng ? nyq_imag<T, N>(Vpart, d, i1, col) : (T)0;
-                cr += odd ? -a_part : a_part;
-                ci = a_self;
+                const cx<T> ab = nyq_pair<T, N>(Vc, d, i1, col, sgn1);
+                const T self = odd ? ab.y : ab.x, part = has_partner ? (odd ? ab.x : ab.y) : (T)0;
+                re += odd ? -part : part;
+                im = self;
             }
             const T F = f[(size_t)i1 * P + col];
-            s[e] = mkc<T>(cr + F, ci);
-            cf[e] = mkc<T>(cr * F, ci * F);
+            sr[e] = re + F;
+            si[e] = im;
+            cr[e] = re * F;
+            ci[e] = im * F;
         }
     }
     T ar[E], ai[E];
@@ -533,6 +547,7 @@ k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__rest
         ai[e] = (T)0;
     }
     const double *Wg = prod_W + (size_t)(g0 + gl) * PPG;
+    const cx<T> *Vp = Vtab + (size_t)(ncu + gl * PPG) * VS;
     for (int p = 0; p < PPG; ++p) {
         const T W = (T)Wg[p];
         if (p + 2 < tiles) prefetch(p + 2);   // buffer of tile p, already read
@@ -540,22 +555,20 @@ k_pass2(const cx<T> *__restrict__ H, const T *__restrict__ Vtab, const T *__rest
         cp_async_wait<1>();
         take(p + 1, v);
         col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
-        const T *Va = Vtab + (size_t)(gl * FPG + prod_local[2 * p]) * VS;
-        const T *Vb = Vtab + (size_t)(gl * FPG + prod_local[2 * p + 1]) * VS;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i1 = t + e * TPL;
             T a = (T)0, b = (T)0;
             if (NYQ) {
-                a = nyq_imag<T, N>(Va, d, i1, col);
-                b = nyq_imag<T, N>(Vb, d, i1, col);
+                const cx<T> ab = nyq_pair<T, N>(Vp + (size_t)p * VS, d, i1, col, sgn1);
+                a = ab.x;
+                b = ab.y;
             }
-            const cx<T> A = mkc<T>(v[e].x + b, a);
-            const cx<T> B = mkc<T>(v[e].y - a, b);
-            const cx<T> X = csub<T>(cmul<T>(A, s[e]), cf[e]);
-            const cx<T> q = cmul<T>(cf[e], A);             // added with a minus sign
-            ar[e] += W * (B.x * X.x - B.y * X.y - q.x);
-            if (IM) ai[e] += W * (B.x * X.y + B.y * X.x - q.y);
+            const T Ar = v[e].x + b, Br = v[e].y - a;          // A = Ar + i a, B = Br + i b
+            const T xr = Ar * sr[e] - a * si[e] - cr[e];       // X = A s - cf
+            const T xi = Ar * si[e] + a * sr[e] - ci[e];
+            ar[e] += W * (Br * xr - b * xi - (cr[e] * Ar - ci[e] * a));
+            if (IM) ai[e] += W * (Br * xi + b * xr - (cr[e] * a + ci[e] * Ar));
         }
     }
     cp_async_wait<0>();

@@ -93,31 +93,32 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
 }
 
 // ------------------------------------------------------------------ Nyquist tables
+// Tables of every unit of chunks [chunk0, chunk0 + nchunks), into p.V.
 template <typename T, int N>
-static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nchunks, cudaStream_t s) {
     typedef LineCfg<T, N> Cfg;
-    const int nfields = ng * hp.fields_per_group;
-    const int field0 = g0 * hp.fields_per_group;
-    const cx<T> *ghat = static_cast<const cx<T> *>(p.ghat);
+    const int upc = chunk_units(hp, hp.groups_per_chunk);
     const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
-    T *V = static_cast<T *>(p.V);
+    cx<T> *V = static_cast<cx<T> *>(p.V);
     const cx<T> *tw = static_cast<const cx<T> *>(p.tw);
+    const cx<T> *ns = static_cast<const cx<T> *>(p.nslice);
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
             const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
             if ((rc = set_smem(k_nyquist_3d<T, N>, smem))) return rc;
-            const int npairs = (nfields + 1) / 2;
-            k_nyquist_3d<T, N><<<dim3(3, npairs), N * Cfg::TPL, smem, s>>>(
-                ph, V, tw, static_cast<const cx<T> *>(p.nslice), field0, nfields, 1);
+            k_nyquist_3d<T, N><<<dim3(3, upc, nchunks), N * Cfg::TPL, smem, s>>>(
+                ph, V, tw, ns, p.prod_local, hp.groups_per_chunk, hp.n_groups, hp.fields_per_group,
+                hp.products_per_group, upc, chunk0);
         } else {
             return (int)cudaErrorInvalidValue;
         }
     } else {
-        const int items = 2 * nfields;
         const size_t smem = (size_t)(N + Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<T>);
         if ((rc = set_smem(k_nyquist_2d<T, N>, smem))) return rc;
-        k_nyquist_2d<T, N><<<(items + Cfg::LPW - 1) / Cfg::LPW, 32, smem, s>>>(ghat, ph, V, tw, field0, items);
+        k_nyquist_2d<T, N><<<dim3((2 * upc + Cfg::LPW - 1) / Cfg::LPW, nchunks), 32, smem, s>>>(
+            ph, V, tw, ns, p.prod_local, hp.groups_per_chunk, hp.n_groups, hp.fields_per_group,
+            hp.products_per_group, upc, chunk0);
     }
     return (int)cudaGetLastError();
 }
@@ -133,9 +134,9 @@ static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cu
     if ((rc = set_smem(k_pass2<T, N, IM, NYQ>, smem))) return rc;
     dim3 grid(P / CB, ng);
     k_pass2<T, N, IM, NYQ><<<grid, CB * Cfg::TPL, smem, s>>>(
-        static_cast<const cx<T> *>(p.H), static_cast<const T *>(p.V), static_cast<const T *>(p.f), p.Qacc,
-        p.Qacc_im, p.prod_local, p.prod_W, static_cast<const cx<T> *>(p.tw), hp.d, P, CB, hp.fields_per_group,
-        hp.products_per_group, g0, ng);
+        static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
+        p.Qacc_im, p.prod_local, p.prod_W, static_cast<const cx<T> *>(p.tw), hp.d, P, CB, hp.products_per_group, g0,
+        ng);
     return (int)cudaGetLastError();
 }
 
@@ -169,13 +170,13 @@ template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int g
     return (int)cudaErrorInvalidValue;
 }
 
-template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nchunks, cudaStream_t s) {
     switch (hp.N) {
-        case 16: return nyquist_n<T, 16>(hp, p, g0, ng, s);
-        case 32: return nyquist_n<T, 32>(hp, p, g0, ng, s);
-        case 64: return nyquist_n<T, 64>(hp, p, g0, ng, s);
-        case 128: return nyquist_n<T, 128>(hp, p, g0, ng, s);
-        case 256: return nyquist_n<T, 256>(hp, p, g0, ng, s);
+        case 16: return nyquist_n<T, 16>(hp, p, chunk0, nchunks, s);
+        case 32: return nyquist_n<T, 32>(hp, p, chunk0, nchunks, s);
+        case 64: return nyquist_n<T, 64>(hp, p, chunk0, nchunks, s);
+        case 128: return nyquist_n<T, 128>(hp, p, chunk0, nchunks, s);
+        case 256: return nyquist_n<T, 256>(hp, p, chunk0, nchunks, s);
     }
     return (int)cudaErrorInvalidValue;
 }

@@ -350,8 +350,8 @@ size_t chunk_unit_bytes(const HostPlan &hp) {
 }
 
 size_t chunk_v_bytes(const HostPlan &hp) {
-    size_t tb = hp.precision == WKE_FP64 ? 8 : 4;
-    return (size_t)hp.groups_per_chunk * hp.fields_per_group * hp.d * (grid_size(hp) / hp.N) * tb;
+    size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;   // a unit's two fields interleaved
+    return (size_t)chunk_units(hp, hp.groups_per_chunk) * hp.d * (grid_size(hp) / hp.N) * cxb;
 }
 
 static size_t grid_size(const HostPlan &hp) {
@@ -367,7 +367,8 @@ size_t plan_device_bytes(const HostPlan &hp) {
     size_t n_fields = (size_t)hp.n_groups * hp.fields_per_group;
     size_t bytes = 0;
     bytes += nd * cxb + hp.d * (nd / hp.N) * cxb;                       // ghat, Nyquist slices
-    bytes += 2 * chunk_unit_bytes(hp) + 2 * chunk_v_bytes(hp);          // H, V double-buffered
+    bytes += 2 * chunk_unit_bytes(hp);                                   // H double-buffered
+    if (hp.nyquist == WKE_NYQ_KEEP) bytes += 2 * chunk_v_bytes(hp);      // Nyquist tables, double-buffered
     bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
     bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
