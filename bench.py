@@ -191,11 +191,13 @@ def run_gpu(args, rank, world, pool, workers):
             torch.distributed.barrier()
         return ms, wall, prof
 
-    # FP32 headline (no per-kernel events in this loop)
+    # FP32 headline (no per-kernel events in this loop); the launch layout is
+    # picked by the library's autotuner before the timed region
     p32 = make("fp32")
     info = p32.info()
     f32 = torch.tensor(f64, dtype=torch.float32, device=dev)
     Q32 = torch.empty_like(f32)
+    tuning, tune_ms = p32.autotune(f32, reps=5) if not args.no_autotune else (wke.wke_plan_get_tuning(p32.handle), 0.0)
     with ClockSampler(dev.index) as clk:
         ms32, wall32, _ = timed(p32, f32, Q32, args.steps, args.warmup)
     clocks = clk.summary()
@@ -204,7 +206,9 @@ def run_gpu(args, rank, world, pool, workers):
     if args.fp32_only:
         line = {"metric": METRIC, "value": round(1000.0 / (sum(ms32) / len(ms32)), 3), "unit": UNIT,
                 "kernels_ms": prof, "plan": {"groups_per_chunk": info.groups_per_chunk,
-                                              "n_chunks": info.n_chunks}, "clocks": clocks}
+                                              "n_chunks": info.n_chunks},
+                "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
+                           "pass1_units_per_block": tuning.pass1_units_per_block}, "clocks": clocks}
         p32.close()
         return line
     t_step = sum(ms32) / len(ms32)
@@ -266,6 +270,8 @@ def run_gpu(args, rank, world, pool, workers):
                 "d2h_bytes_per_step": qh.numel() * 4},
         "gpu_launches": args.steps * info.launches_per_collision,
         "clocks": clocks, "roofline": roofline,
+        "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
+                   "pass1_units_per_block": tuning.pass1_units_per_block, "autotune_ms": round(tune_ms, 4)},
         "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
                  "fields_per_group": info.fields_per_group, "products_per_group": info.products_per_group,
                  "flops_per_eval": info.flops_per_collision, "l2_bytes_per_eval": info.l2_bytes_per_collision},
@@ -339,6 +345,7 @@ def main():
     ap.add_argument("--oracle-nodes", type=int, default=16,
                     help="oracle nodes per host process per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch layout")
     ap.add_argument("--fp32-only", action="store_true",
                     help="only the FP32 timing and kernel split (profiling runs)")
     ap.add_argument("--chunk-mb", type=float, default=0.0,

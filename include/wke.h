@@ -186,6 +186,32 @@ int wke_step(wke_plan *plan, void *f_dev, double dt, int rk_stages);
  * a device pointer to d + 2 doubles.  Asynchronous on `stream`. */
 int wke_moments(wke_plan *plan, const void *g_dev, double *out_dev, void *stream);
 
+/* Launch layout of a plan's kernels.  Layouts change speed, not results
+ * beyond rounding. */
+typedef struct wke_tuning {
+    int pass2_points_per_thread;   /* axis-0 transform in pass 2: 4 (radices
+                                      4,4,4 at N = 64: fewer registers, more
+                                      blocks per SM) or 8 (radices 8,8: fewer
+                                      instructions); N >= 128 always uses 8 */
+    int pass1_units_per_block;     /* units each pass-1 block transforms for its
+                                      plane (reuses the plane's coefficients);
+                                      0 = automatic */
+} wke_tuning;
+
+int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out);
+
+/* Set the layout; WKE_ERR_INVALID for values out of range.  Drops the plan's
+ * cached graphs (the next call re-captures). */
+int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *tuning);
+
+/* Autotuner: times every candidate layout on this plan's own workload
+ * (f_dev in, Q_dev out, both device buffers of the plan's grid), `reps`
+ * evaluations each after one warm-up, with CUDA events on the plan's stream,
+ * and keeps the fastest.  chosen (may be NULL) receives it and best_ms (may
+ * be NULL) its milliseconds per evaluation.  Synchronises the plan's stream. */
+int wke_plan_autotune(wke_plan *plan, const void *f_dev, void *Q_dev, int reps, wke_tuning *chosen,
+                      double *best_ms);
+
 /* Evaluations are captured into a CUDA graph per distinct (f, Q, Qim)
  * pointer set on first use and replayed afterwards (default on; at most 8
  * graphs per plan).  enable = 0 launches every kernel directly instead.  A

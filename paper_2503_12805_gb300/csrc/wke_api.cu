@@ -547,6 +547,70 @@ int wke_moments(wke_plan *plan, const void *g, double *out, void *stream) {
     return WKE_OK;
 }
 
+int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out) {
+    if (!plan || !out) return fail(WKE_ERR_INVALID, "plan and out must be non-NULL");
+    out->pass2_points_per_thread = plan->hp.N >= 128 ? 8 : plan->hp.tune_p2_points;
+    out->pass1_units_per_block = plan->hp.tune_p1_units_per_block;
+    return WKE_OK;
+}
+
+int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
+    if (!plan || !t) return fail(WKE_ERR_INVALID, "plan and tuning must be non-NULL");
+    if (t->pass2_points_per_thread != 4 && t->pass2_points_per_thread != 8)
+        return fail(WKE_ERR_INVALID, "pass2_points_per_thread must be 4 or 8");
+    if (t->pass1_units_per_block < 0 || t->pass1_units_per_block > chunk_units(plan->hp, plan->hp.groups_per_chunk))
+        return fail(WKE_ERR_INVALID, "pass1_units_per_block must be 0..units per chunk");
+    plan->hp.tune_p2_points = t->pass2_points_per_thread;
+    plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
+    free_graphs(plan);
+    return WKE_OK;
+}
+
+int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuning *chosen, double *best_ms) {
+    if (!plan || !f || !Q || reps < 1) return fail(WKE_ERR_INVALID, "plan, f, Q and reps >= 1 are required");
+    const HostPlan &hp = plan->hp;
+    std::vector<wke_tuning> cands;
+    const int p2s[2] = {4, 8};
+    const int upc = chunk_units(hp, hp.groups_per_chunk);
+    const int p1s[4] = {0, 1, 2, 3};
+    for (int a = 0; a < (hp.N <= 64 ? 2 : 1); ++a)
+        for (int b = 0; b < (hp.d == 3 ? 4 : 1); ++b)
+            if (p1s[b] <= upc) cands.push_back(wke_tuning{hp.N >= 128 ? 8 : p2s[a], p1s[b]});
+    cudaStream_t s = plan->stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "autotune events");
+    wke_tuning best = cands[0];
+    double best_t = 1e300;
+    int rc = WKE_OK;
+    for (const wke_tuning &c : cands) {
+        if ((rc = wke_plan_set_tuning(plan, &c))) break;
+        if ((rc = collision(plan, f, Q, nullptr, s))) break;      // warm-up (and graph capture)
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !rc; ++r) rc = collision(plan, f, Q, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (rc) break;
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / reps < best_t) {
+            best_t = ms / reps;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = wke_plan_set_tuning(plan, &best))) return rc;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
+    return WKE_OK;
+}
+
 int wke_plan_use_graphs(wke_plan *plan, int enable) {
     if (!plan) return fail(WKE_ERR_INVALID, "plan is NULL");
     plan->use_graphs = enable != 0;

@@ -51,6 +51,10 @@ struct HostPlan {
     size_t chunk_bytes = 0;
 
     double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)
+
+    // Launch layout (wke_plan_set_tuning / wke_plan_autotune).
+    int tune_p2_points = 8;              // pass-2 points per thread (4 or 8; N >= 128 uses 8)
+    int tune_p1_units_per_block = 0;     // pass-1 units per block (0 = automatic: 3)
 };
 
 // Validate arguments and fill `hp` (no device work).  Returns WKE_OK or an

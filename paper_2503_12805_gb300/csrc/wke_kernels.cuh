@@ -424,8 +424,11 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
 // A B (C + F) - C F (A + B) = B (A s - cf) - cf A.  Only one transformed
 // field is live at a time.  The group's sum goes to that group's double
 // accumulator.
-template <typename T, int N> struct Pass2Cfg {
-    static constexpr int E = N <= 64 ? 4 : 8;           // points per thread
+// Points per thread EP: 4 (radices 4, 4, 4 for N = 64; fewer registers, more
+// blocks per SM) or 8 (radices 8, 8; fewer instructions).  The plan's tuning
+// picks one; N >= 128 always uses 8 so a column fits in one warp.
+template <typename T, int N, int EP> struct Pass2Cfg {
+    static constexpr int E = N >= 128 ? 8 : EP;
     static constexpr int TPL = N / E;                    // threads per column
     static constexpr int THREADS = 256;
     static constexpr int CB = THREADS / TPL;             // columns per block (at most)
@@ -474,13 +477,13 @@ __device__ __forceinline__ cx<T> nyq_pair(const cx<T> *__restrict__ Vu, int d, i
 //   real-slot field = (Re Z + b) + i a,  imaginary-slot field = (Im Z - a) + i b.
 // Then, keeping s = C + F and cf = C F, each product contributes
 // A B (C + F) - C F (A + B) = B (A s - cf) - cf A, written out in real parts.
-template <typename T, int N, bool IM, bool NYQ>
-__global__ void __launch_bounds__(Pass2Cfg<T, N>::THREADS, Pass2Cfg<T, N>::MIN_BLOCKS)
+template <typename T, int N, int EP, bool IM, bool NYQ>
+__global__ void __launch_bounds__(Pass2Cfg<T, N, EP>::THREADS, Pass2Cfg<T, N, EP>::MIN_BLOCKS)
 k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
         double *__restrict__ Qacc, double *__restrict__ Qim, const int *__restrict__ prod_local,
         const double *__restrict__ prod_W, const cx<T> *__restrict__ tw_g, int d, int P, int CB, int PPG, int g0,
         int ng) {
-    typedef Pass2Cfg<T, N> Cfg;
+    typedef Pass2Cfg<T, N, EP> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);

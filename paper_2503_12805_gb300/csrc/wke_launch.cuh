@@ -74,7 +74,7 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
             const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
             if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
             // enough blocks to fill the GPU several times over
-            const int upb = std::max(1, std::min(nunits, nunits * N / 1200));
+            const int upb = std::min(nunits, hp.tune_p1_units_per_block > 0 ? hp.tune_p1_units_per_block : 3);
             dim3 grid(N, (nunits + upb - 1) / upb);
             k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng,
                                                                hp.fields_per_group, hp.products_per_group, nunits, upb);
@@ -124,27 +124,36 @@ static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nc
 }
 
 // ------------------------------------------------------------------ pass 2
-template <typename T, int N, bool IM, bool NYQ>
+template <typename T, int N, int EP, bool IM, bool NYQ>
 static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
-    typedef Pass2Cfg<T, N> Cfg;
+    typedef Pass2Cfg<T, N, EP> Cfg;
     const int P = cols_of(hp);
     const int CB = std::min(Cfg::CB, P);       // columns per block
     const size_t smem = (size_t)(N + LinePad<N>::LEN * CB + 2 * N * CB) * sizeof(cx<T>);
     int rc = 0;
-    if ((rc = set_smem(k_pass2<T, N, IM, NYQ>, smem))) return rc;
+    if ((rc = set_smem(k_pass2<T, N, EP, IM, NYQ>, smem))) return rc;
     dim3 grid(P / CB, ng);
-    k_pass2<T, N, IM, NYQ><<<grid, CB * Cfg::TPL, smem, s>>>(
+    k_pass2<T, N, EP, IM, NYQ><<<grid, CB * Cfg::TPL, smem, s>>>(
         static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
         p.Qacc_im, p.prod_local, p.prod_W, static_cast<const cx<T> *>(p.tw), hp.d, P, CB, hp.products_per_group, g0,
         ng);
     return (int)cudaGetLastError();
 }
 
+template <typename T, int N, int EP>
+static int pass2_ne(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
+    if (nyq)
+        return im ? pass2_nim<T, N, EP, true, true>(hp, p, g0, ng, s) : pass2_nim<T, N, EP, false, true>(hp, p, g0, ng, s);
+    return im ? pass2_nim<T, N, EP, true, false>(hp, p, g0, ng, s) : pass2_nim<T, N, EP, false, false>(hp, p, g0, ng, s);
+}
+
 template <typename T, int N>
 static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
-    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
-    if (nyq) return im ? pass2_nim<T, N, true, true>(hp, p, g0, ng, s) : pass2_nim<T, N, false, true>(hp, p, g0, ng, s);
-    return im ? pass2_nim<T, N, true, false>(hp, p, g0, ng, s) : pass2_nim<T, N, false, false>(hp, p, g0, ng, s);
+    if constexpr (N <= 64) {
+        if (hp.tune_p2_points == 8) return pass2_ne<T, N, 8>(hp, p, g0, ng, im, s);
+    }
+    return pass2_ne<T, N, 4>(hp, p, g0, ng, im, s);
 }
 
 // ------------------------------------------------------------------ dispatch on N

@@ -48,6 +48,10 @@ class WkeQuadrature(ctypes.Structure):
     ]
 
 
+class WkeTuning(ctypes.Structure):
+    _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int)]
+
+
 class WkePlanInfo(ctypes.Structure):
     _fields_ = [
         ("d", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int), ("precision", ctypes.c_int),
@@ -63,7 +67,8 @@ EXPORTED = [
     "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
     "wke_plan_get_info", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
-    "wke_moments_noalloc", "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
+    "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
+    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
 ]
 PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist")
 
@@ -88,6 +93,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_step": (i, [vp, vp, d, i]),
         "wke_moments": (i, [vp, vp, vp, vp]),
         "wke_moments_noalloc": (i, [i, i, d, i, vp, vp, vp]),
+        "wke_plan_get_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
+        "wke_plan_set_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
+        "wke_plan_autotune": (i, [vp, vp, vp, i, ctypes.POINTER(WkeTuning), ctypes.POINTER(ctypes.c_double)]),
         "wke_plan_use_graphs": (i, [vp, i]),
         "wke_plan_profile": (i, [vp, i]),
         "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
@@ -181,6 +189,26 @@ def wke_moments_noalloc(d: int, N: int, L: float, precision: int, g_ptr: int, ou
     """Plan-free moments for callers that cannot allocate device memory; the
     partial sums live in a fixed array inside the library (see wke.h)."""
     _check(lib().wke_moments_noalloc(d, N, L, precision, g_ptr, out_ptr, stream))
+
+
+def wke_plan_get_tuning(plan) -> WkeTuning:
+    t = WkeTuning()
+    _check(lib().wke_plan_get_tuning(plan, ctypes.byref(t)))
+    return t
+
+
+def wke_plan_set_tuning(plan, pass2_points_per_thread: int, pass1_units_per_block: int = 0) -> None:
+    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block)
+    _check(lib().wke_plan_set_tuning(plan, ctypes.byref(t)))
+
+
+def wke_plan_autotune(plan, f_ptr: int, Q_ptr: int, reps: int = 5):
+    """Time the candidate layouts on this plan and keep the fastest;
+    returns (tuning, ms per evaluation)."""
+    t = WkeTuning()
+    ms = ctypes.c_double()
+    _check(lib().wke_plan_autotune(plan, f_ptr, Q_ptr, reps, ctypes.byref(t), ctypes.byref(ms)))
+    return t, ms.value
 
 
 def wke_plan_use_graphs(plan, enable: bool) -> None:
@@ -295,6 +323,14 @@ class Plan:
         s = (stream or torch.cuda.current_stream()).cuda_stream
         wke_moments(self.handle, g.data_ptr(), out.data_ptr(), s)
         return out
+
+    def autotune(self, f, reps: int = 5):
+        """Pick the fastest launch layout for this plan on input f."""
+        import torch
+        self._check_grid(f)
+        Q = torch.empty_like(f)
+        wke_plan_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
+        return wke_plan_autotune(self.handle, f.data_ptr(), Q.data_ptr(), reps)
 
     def collision_host(self, f_host, Q_host):
         """f_host, Q_host: CPU tensors (pinned for full bandwidth) of the plan dtype."""

@@ -243,3 +243,26 @@ def test_graph_replay_matches_direct_launches():
     for g_rep in graph:
         for a, b in zip(g_rep, direct):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_launch_layout_matches_oracle(prec):
+    """Each layout the autotuner may pick computes the same Q (to rounding);
+    the autotuner returns one of them."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.gaussian_noise(3, 32, 8.0, 55, 0.1)
+    ref, _ = O.collision_fast(f, 8.0, _oracle_quad(3, 8.0, 3, 8, 8, "cube"))
+    with _plan(wke, 3, 32, 8.0, 3, 8, 8, "cube", precision=prec) as plan:
+        for p2 in (4, 8):
+            for p1 in (0, 1, 2, 3):
+                wke.wke_plan_set_tuning(plan.handle, p2, p1)
+                Q = gpu_collision(torch, plan, f)
+                assert rel_max_err(Q, ref) <= TOL[prec], (p2, p1)
+        ft = torch.tensor(f, dtype=plan.dtype, device="cuda")
+        tuning, ms = plan.autotune(ft, reps=2)
+        assert tuning.pass2_points_per_thread in (4, 8) and ms > 0
+        Q = gpu_collision(torch, plan, f)
+        assert rel_max_err(Q, ref) <= TOL[prec]
+        with pytest.raises(wke.WkeError):
+            wke.wke_plan_set_tuning(plan.handle, 6, 0)
