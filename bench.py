@@ -276,6 +276,8 @@ def run_gpu(args, rank, world, pool, workers):
                  "fields_per_group": info.fields_per_group, "products_per_group": info.products_per_group,
                  "flops_per_eval": info.flops_per_collision, "l2_bytes_per_eval": info.l2_bytes_per_collision},
     }
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(args.serve_requests, I.BASE_SEED + 4 + rank, wke, 40 << 30, 8)
     if rank == 0 and pool is not None:
         rate, wall, nodes = cpu_oracle_rate(pool, args.oracle_nodes, workers)
         line["cpu_baseline"] = {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
@@ -307,6 +309,61 @@ def kernel_flops(cls, info):
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * G * nd
+
+
+# ------------------------------------------------------------------ serving
+
+SERVE_RATE = 200.0      # mean arrivals per second (Poisson)
+
+
+def serving_mix():
+    """(d, N, n_r, n_s, n_sig) of the mixed stream: 2D N in {64, 128, 256}
+    with M = 4N (N/4 x 4 x 4) and 3D N in {32, 64} with M = 32N (N/2 x 8 x 8);
+    3D N = 48 needs radix-3 transforms, which this build does not have."""
+    return [s for s in I.serving_request_sizes() if not (s[0] == 3 and s[1] == 48)]
+
+
+def _serving_initial(d, N, seed):
+    if d == 2:
+        return I.two_gaussians(N, 8.0, seed)
+    return I.ring(3, N, 8.0) if seed % 2 else I.gaussian_noise(3, N, 8.0, seed)
+
+
+def run_serving(n_requests, seed, wke, budget_bytes, max_active):
+    """Poisson stream at SERVE_RATE req/s of mixed requests (1-20 RK4 steps,
+    dt = 1e-3, FP32) through the continuous-batching server; latency is
+    completion minus submission on the server's clock."""
+    import numpy as np
+    sizes = serving_mix()
+    u = I.splitmix64_uniform(seed, 3 * n_requests)
+    gaps = -np.log(1.0 - u[0::3]) / SERVE_RATE
+    arrive = np.cumsum(gaps)
+    reqs = []
+    for k in range(n_requests):
+        d, N, n_r, n_s, n_sig = sizes[int(u[3 * k + 1] * len(sizes))]
+        steps = 1 + int(u[3 * k + 2] * 20)
+        reqs.append((d, N, n_r, n_s, n_sig, steps, _serving_initial(d, N, seed + k).astype(np.float32)))
+    srv = wke.Server(device_budget_bytes=budget_bytes, max_active=max_active)
+    try:
+        t0 = time.perf_counter()
+        ids = []
+        for k, (d, N, n_r, n_s, n_sig, steps, f) in enumerate(reqs):
+            delay = arrive[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(f, n_r, n_s, n_sig, steps, 1e-3)[0])
+        stats = [srv.wait(i, timeout_s=600) for i in ids]
+    finally:
+        srv.close()
+    ok = [st for st in stats if st.status == wke.WKE_OK]
+    lat = np.array([st.t_done - st.t_submit for st in ok]) * 1000.0
+    span = max(st.t_done for st in ok) - min(st.t_submit for st in ok)
+    evals = sum(4 * r[5] for r in reqs)
+    return {"requests": n_requests, "completed": len(ok), "arrival_rate_req_s": SERVE_RATE,
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "throughput_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2),
+            "max_active": max_active, "budget_gib": round(budget_bytes / 2 ** 30, 1),
+            "mix": "2D N in {64,128,256} (M=4N), 3D N in {32,64} (M=32N); steps U{1..20} RK4, dt=1e-3, FP32"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -346,6 +403,8 @@ def main():
                     help="oracle nodes per host process per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch layout")
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="requests in the serving stream (0: skip serving)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="only the FP32 timing and kernel split (profiling runs)")
     ap.add_argument("--chunk-mb", type=float, default=0.0,

@@ -50,6 +50,7 @@ extern "C" {
 #define WKE_ERR_OOM           -2   /* device or host allocation failed        */
 #define WKE_ERR_CUDA          -3   /* a CUDA runtime call or launch failed    */
 #define WKE_ERR_UNSUPPORTED   -4   /* valid request this build does not serve */
+#define WKE_CANCELLED         -5   /* a served request was cancelled before it ran */
 
 /* ------------------------------------------------------------ enumerations */
 /* Sphere rules (Sec. 3.3: mid-point in 2D, spherical designs in 3D). */
@@ -247,6 +248,56 @@ int wke_plan_profile_read(wke_plan *plan, double *out_host);
  * the GPU race, so order them (one stream, or events). */
 int wke_moments_noalloc(int d, int N, double L, int precision, const void *g_dev, double *out_dev,
                         void *stream);
+
+/* ------------------------------------------------------------ serving */
+/* A serving loop runs time-stepping requests of mixed sizes from concurrent
+ * simulations with continuous batching: a worker thread admits the oldest
+ * pending request as soon as fewer than `max_active` requests run and its
+ * device footprint (wke_plan_footprint_bytes plus its grid) fits within
+ * `device_budget_bytes`, then enqueues all of its steps on its own stream,
+ * so requests overlap on the GPU.  Plans of finished requests stay resident
+ * and are reused by later requests of the same shape; idle plans are evicted
+ * least recently used first when memory is needed.  Results are identical to
+ * running the same steps alone (the kernels sum in a fixed order). */
+typedef struct wke_server wke_server;
+
+typedef struct wke_request {
+    int d, N;              /* grid (see wke_plan_create)                      */
+    double L;
+    int n_r, n_s, n_sig;   /* quadrature counts, default rules                */
+    int precision;         /* WKE_FP32 or WKE_FP64                            */
+    int rk_stages;         /* 1, 2 or 4 (see wke_step)                        */
+    int steps;             /* number of time steps                            */
+    double dt;             /* step size                                       */
+    const void *f_host;    /* initial grid, read when the request is admitted  */
+    void *out_host;        /* final grid, written when the request completes   */
+} wke_request;
+
+typedef struct wke_request_stats {
+    long long id;
+    int status;            /* WKE_OK, WKE_CANCELLED or a WKE_ERR_* code       */
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock      */
+} wke_request_stats;
+
+/* Start a server on the current device.  The worker thread makes every CUDA
+ * call of the server. */
+int wke_server_create(size_t device_budget_bytes, int max_active, wke_server **out);
+
+/* Queue a request (any thread); the descriptor is copied, the host buffers
+ * must stay valid until the request completes.  *id receives its id.  A
+ * request whose footprint exceeds the whole budget completes with
+ * WKE_ERR_OOM. */
+int wke_server_submit(wke_server *server, const wke_request *request, long long *id);
+
+/* Cancel a request that has not been admitted yet (WKE_ERR_INVALID otherwise). */
+int wke_server_cancel(wke_server *server, long long id);
+
+/* Block until request `id` completes (timeout_s < 0: no limit) and fill
+ * *stats.  WKE_ERR_INVALID on an unknown id or a timeout. */
+int wke_server_wait(wke_server *server, long long id, double timeout_s, wke_request_stats *stats);
+
+/* Finish every queued request, stop the worker and release all memory. */
+int wke_server_destroy(wke_server *server);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *wke_last_error_string(void);

@@ -19,6 +19,7 @@ WKE_ERR_INVALID = -1
 WKE_ERR_OOM = -2
 WKE_ERR_CUDA = -3
 WKE_ERR_UNSUPPORTED = -4
+WKE_CANCELLED = -5
 
 WKE_SPHERE_DEFAULT = -1
 WKE_SPHERE_MIDPOINT_2D = 0
@@ -52,6 +53,18 @@ class WkeTuning(ctypes.Structure):
     _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int)]
 
 
+class WkeRequest(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int), ("L", ctypes.c_double),
+                ("n_r", ctypes.c_int), ("n_s", ctypes.c_int), ("n_sig", ctypes.c_int),
+                ("precision", ctypes.c_int), ("rk_stages", ctypes.c_int), ("steps", ctypes.c_int),
+                ("dt", ctypes.c_double), ("f_host", ctypes.c_void_p), ("out_host", ctypes.c_void_p)]
+
+
+class WkeRequestStats(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class WkePlanInfo(ctypes.Structure):
     _fields_ = [
         ("d", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int), ("precision", ctypes.c_int),
@@ -67,6 +80,7 @@ EXPORTED = [
     "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
     "wke_plan_get_info", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
+    "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
     "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
 ]
@@ -93,6 +107,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_step": (i, [vp, vp, d, i]),
         "wke_moments": (i, [vp, vp, vp, vp]),
         "wke_moments_noalloc": (i, [i, i, d, i, vp, vp, vp]),
+        "wke_server_create": (i, [sz, i, ctypes.POINTER(vp)]),
+        "wke_server_submit": (i, [vp, ctypes.POINTER(WkeRequest), ctypes.POINTER(ctypes.c_longlong)]),
+        "wke_server_cancel": (i, [vp, ctypes.c_longlong]),
+        "wke_server_wait": (i, [vp, ctypes.c_longlong, d, ctypes.POINTER(WkeRequestStats)]),
+        "wke_server_destroy": (i, [vp]),
         "wke_plan_get_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
         "wke_plan_set_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
         "wke_plan_autotune": (i, [vp, vp, vp, i, ctypes.POINTER(WkeTuning), ctypes.POINTER(ctypes.c_double)]),
@@ -224,6 +243,73 @@ def wke_plan_profile_read(plan) -> dict:
     out = (ctypes.c_double * (2 * len(PROF_CLASSES)))()
     _check(lib().wke_plan_profile_read(plan, out))
     return {c: (out[2 * i], int(out[2 * i + 1])) for i, c in enumerate(PROF_CLASSES)}
+
+
+def wke_server_create(device_budget_bytes: int, max_active: int):
+    out = ctypes.c_void_p()
+    _check(lib().wke_server_create(device_budget_bytes, max_active, ctypes.byref(out)))
+    return out
+
+
+def wke_server_submit(server, request: WkeRequest) -> int:
+    rid = ctypes.c_longlong()
+    _check(lib().wke_server_submit(server, ctypes.byref(request), ctypes.byref(rid)))
+    return rid.value
+
+
+def wke_server_cancel(server, rid: int) -> None:
+    _check(lib().wke_server_cancel(server, rid))
+
+
+def wke_server_wait(server, rid: int, timeout_s: float = -1.0) -> WkeRequestStats:
+    st = WkeRequestStats()
+    _check(lib().wke_server_wait(server, rid, timeout_s, ctypes.byref(st)))
+    return st
+
+
+def wke_server_destroy(server) -> None:
+    _check(lib().wke_server_destroy(server))
+
+
+class Server:
+    """Continuous-batching server; requests carry numpy host arrays."""
+
+    def __init__(self, device_budget_bytes: int, max_active: int = 8):
+        self.handle = wke_server_create(device_budget_bytes, max_active)
+        self._keep = {}
+
+    def submit(self, f, n_r, n_s, n_sig, steps, dt, L=8.0, rk_stages=4, precision="fp32"):
+        """Queue f (numpy, shape (N,)*d, float32 or float64 per precision);
+        returns (request id, output array filled on completion)."""
+        import numpy as np
+        dtype = np.float32 if precision == "fp32" else np.float64
+        f = np.ascontiguousarray(f, dtype=dtype)
+        out = np.empty_like(f)
+        req = WkeRequest(f.ndim, f.shape[0], L, n_r, n_s, n_sig,
+                         WKE_FP32 if precision == "fp32" else WKE_FP64, rk_stages, steps, dt,
+                         f.ctypes.data, out.ctypes.data)
+        rid = wke_server_submit(self.handle, req)
+        self._keep[rid] = (f, out)
+        return rid, out
+
+    def cancel(self, rid: int) -> None:
+        wke_server_cancel(self.handle, rid)
+
+    def wait(self, rid: int, timeout_s: float = -1.0) -> WkeRequestStats:
+        st = wke_server_wait(self.handle, rid, timeout_s)
+        self._keep.pop(rid, None)
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wke_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ------------------------------------------------------------ torch helper

@@ -1,0 +1,78 @@
+"""Serving loop: continuous batching of time-stepping requests.
+
+Each request's result must be the same when it runs alone and when it runs
+in a mix with other requests overlapping on the GPU; requests that cannot fit
+the device budget are rejected without affecting the others; a cancelled
+request does not disturb the rest of the stream.
+"""
+import numpy as np
+import pytest
+
+import wke_inputs as I
+from tests.gpu_util import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+# (d, N, n_r, n_s, n_sig, steps, generator)
+MIX = [
+    (2, 64, 16, 4, 4, 3, lambda: I.two_gaussians(64, 8.0, 1)),
+    (3, 32, 8, 8, 8, 2, lambda: I.gaussian_noise(3, 32, 8.0, 2)),
+    (2, 128, 8, 4, 4, 4, lambda: I.two_gaussians(128, 8.0, 3)),
+    (3, 16, 8, 8, 8, 5, lambda: I.ring(3, 16, 8.0)),
+    (2, 64, 16, 4, 4, 2, lambda: I.gaussian_noise(2, 64, 8.0, 4, 0.05)),
+    (3, 32, 8, 8, 8, 1, lambda: I.ring(3, 32, 8.0)),
+]
+
+
+def _alone(torch, wke, d, N, n_r, n_s, n_sig, steps, f, dt=1e-3):
+    with wke.Plan(d, N, 8.0, n_r, n_s, n_sig, precision="fp32") as plan:
+        ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+        for _ in range(steps):
+            plan.step(ft, dt, 4)
+        torch.cuda.synchronize()
+        return ft.cpu().numpy()
+
+
+def test_results_same_alone_and_in_the_mix():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    inputs = [gen().astype(np.float32) for *_, gen in MIX]
+    with wke.Server(device_budget_bytes=8 << 30, max_active=4) as srv:
+        subs = [srv.submit(f, n_r, n_s, n_sig, steps, 1e-3) for (d, N, n_r, n_s, n_sig, steps, _), f in zip(MIX, inputs)]
+        stats = [srv.wait(rid, timeout_s=120) for rid, _ in subs]
+    assert all(st.status == wke.WKE_OK for st in stats)
+    for (d, N, n_r, n_s, n_sig, steps, _), f, (rid, out) in zip(MIX, inputs, subs):
+        ref = _alone(torch, wke, d, N, n_r, n_s, n_sig, steps, f)
+        assert np.array_equal(out, ref), (d, N)
+        assert not np.array_equal(out, f)               # the steps did change f
+
+
+def test_oversize_request_rejected_others_unaffected():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    small = I.two_gaussians(64, 8.0, 9).astype(np.float32)
+    big = I.ring(3, 64, 8.0).astype(np.float32)
+    with wke.Server(device_budget_bytes=64 << 20, max_active=2) as srv:
+        rid_big, _ = srv.submit(big, 32, 8, 8, 1, 1e-3)
+        rid_small, out = srv.submit(small, 16, 4, 4, 2, 1e-3)
+        st_big = srv.wait(rid_big, timeout_s=60)
+        st_small = srv.wait(rid_small, timeout_s=60)
+    assert st_big.status == wke.WKE_ERR_OOM
+    assert st_small.status == wke.WKE_OK
+    assert np.array_equal(out, _alone(torch, wke, 2, 64, 16, 4, 4, 2, small))
+
+
+def test_cancelled_request_does_not_disturb_the_stream():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    fs = [I.two_gaussians(64, 8.0, s).astype(np.float32) for s in (11, 12, 13)]
+    with wke.Server(device_budget_bytes=4 << 30, max_active=1) as srv:
+        r0, o0 = srv.submit(fs[0], 16, 4, 4, 20, 1e-3)
+        r1, _ = srv.submit(fs[1], 16, 4, 4, 20, 1e-3)
+        r2, o2 = srv.submit(fs[2], 16, 4, 4, 3, 1e-3)
+        srv.cancel(r1)
+        st = [srv.wait(r, timeout_s=120) for r in (r0, r1, r2)]
+    assert [s.status for s in st] == [wke.WKE_OK, wke.WKE_CANCELLED, wke.WKE_OK]
+    assert np.array_equal(o0, _alone(torch, wke, 2, 64, 16, 4, 4, 20, fs[0]))
+    assert np.array_equal(o2, _alone(torch, wke, 2, 64, 16, 4, 4, 3, fs[2]))
+    assert st[2].t_admit >= st[0].t_submit
