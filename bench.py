@@ -276,6 +276,8 @@ def run_gpu(args, rank, world, pool, workers):
                  "fields_per_group": info.fields_per_group, "products_per_group": info.products_per_group,
                  "flops_per_eval": info.flops_per_collision, "l2_bytes_per_eval": info.l2_bytes_per_collision},
     }
+    if args.rk:
+        line["time_stepping"] = run_time_stepping(wke, torch, dev)
     if args.serve_requests > 0:
         line["serving"] = run_serving(args.serve_requests, I.BASE_SEED + 4 + rank, wke, 40 << 30, 8)
     if rank == 0 and pool is not None:
@@ -309,6 +311,51 @@ def kernel_flops(cls, info):
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * G * nd
+
+
+# ------------------------------------------------------------------ time stepping
+
+def run_time_stepping(wke, torch, dev):
+    """RK4 on 2D N=128, M=512 (two Gaussians, 200 steps, dt = 1e-3) and RK2
+    on 3D N=64, M=2048 (ring, 50 steps).  The ring's collision term reaches
+    |Q| ~ 770 at max f = 1, so explicit steps of 1e-3 blow up within tens of
+    steps; its run uses dt = 1e-5.  Reports steps/s (CUDA events around the
+    steps; each step is one graph launch), the relative drift of mass and
+    energy, and the FP32-FP64 difference after the FP64 run's steps."""
+    out = {}
+    cases = [("2d_n128_m512_rk4", I.WORKLOADS["2d_n128_m512"], 4, 1e-3, 200, 200),
+             ("3d_n64_m2048_rk2", WORKLOAD, 2, 1e-5, 50, 10)]
+    for name, w, stages, dt, steps32, steps64 in cases:
+        res, snap = {"dt": dt}, {}
+        for prec, steps in (("fp64", steps64), ("fp32", steps32)):
+            plan = wke.Plan(w.d, w.N, w.L, w.n_r, w.n_s, w.n_sig, sphere=w.sphere, precision=prec)
+            ft = torch.tensor(w.initial(), dtype=plan.dtype, device=dev)
+            m0 = plan.moments(ft).cpu().numpy()
+            ms = 0.0
+            done = 0
+            for seg in (steps64, steps - steps64):
+                if seg <= 0:
+                    continue
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record()
+                for _ in range(seg):
+                    plan.step(ft, dt, stages)
+                b.record()
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+                done += seg
+                if done == steps64:
+                    snap[prec] = ft.double()
+            m1 = plan.moments(ft).cpu().numpy()
+            res[prec] = {"steps": steps, "steps_per_s": round(steps * 1000.0 / ms, 3),
+                         "mass_drift": float(abs(m1[0] - m0[0]) / abs(m0[0])),
+                         "energy_drift": float(abs(m1[-1] - m0[-1]) / abs(m0[-1]))}
+            plan.close()
+        diff = (snap["fp32"] - snap["fp64"]).abs().max() / snap["fp64"].abs().max()
+        res["fp32_vs_fp64_rel_diff_after_%d_steps" % steps64] = float(diff)
+        out[name] = res
+    return out
 
 
 # ------------------------------------------------------------------ serving
@@ -403,6 +450,7 @@ def main():
                     help="oracle nodes per host process per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch layout")
+    ap.add_argument("--no-rk", dest="rk", action="store_false", help="skip the time-stepping section")
     ap.add_argument("--serve-requests", type=int, default=120,
                     help="requests in the serving stream (0: skip serving)")
     ap.add_argument("--fp32-only", action="store_true",

@@ -178,7 +178,10 @@ int wke_plan_set_stream(wke_plan *plan, void *stream);
 /* One explicit Runge-Kutta step of df/dt = Q(f) on the grid values (the
  * paper integrates with RK4, Sec. 4): rk_stages 1 = forward Euler, 2 = Heun,
  * 4 = classical RK4.  f_dev is updated in place on the plan's stream;
- * asynchronous.  Errors: WKE_ERR_INVALID for other rk_stages or dt not finite. */
+ * asynchronous.  With graphs on (the default) the whole step - every
+ * stage's evaluation and stage update - is captured once per (f_dev, dt,
+ * rk_stages) and replayed as one graph launch.  Errors: WKE_ERR_INVALID for
+ * other rk_stages or dt not finite. */
 int wke_step(wke_plan *plan, void *f_dev, double dt, int rk_stages);
 
 /* Macroscopic moments of a grid function g (Sec. 2): out_dev[0] = h^d sum g

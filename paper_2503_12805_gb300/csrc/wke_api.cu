@@ -41,6 +41,15 @@ struct GraphEntry {
     unsigned long long used;
 };
 
+// An instantiated graph of one Runge-Kutta step for a given (f, dt, stages).
+struct StepGraph {
+    void *f;
+    double dt;
+    int stages;
+    cudaGraphExec_t exec;
+    unsigned long long used;
+};
+
 struct wke_plan {
     HostPlan hp;
     DevicePtrs dp{};
@@ -53,6 +62,7 @@ struct wke_plan {
     cudaEvent_t ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr}, ev_nq[2] = {nullptr, nullptr};
     bool use_graphs = true;
     std::vector<GraphEntry> graphs;
+    std::vector<StepGraph> step_graphs;
     unsigned long long tick = 0;
     std::vector<void *> allocs;
     void *f_stage = nullptr, *Q_stage = nullptr;   // wke_collision_host buffers
@@ -93,6 +103,8 @@ int dev_alloc(wke_plan *p, void **ptr, size_t bytes) {
 void free_graphs(wke_plan *p) {
     for (GraphEntry &g : p->graphs) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
+    for (StepGraph &g : p->step_graphs) cudaGraphExecDestroy(g.exec);
+    p->step_graphs.clear();
 }
 
 void free_plan(wke_plan *p) {
@@ -499,42 +511,96 @@ int wke_plan_set_stream(wke_plan *plan, void *stream) {
     return WKE_OK;
 }
 
+// Butcher tableaux: b (weights) and c (node of the next stage) for forward
+// Euler, Heun and classical RK4.
+static bool rk_tableau(int stages, const double **b, const double **c) {
+    static const double b1[1] = {1.0}, c1[1] = {0.0};
+    static const double b2[2] = {0.5, 0.5}, c2[2] = {1.0, 0.0};
+    static const double b4[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, c4[4] = {0.5, 0.5, 1.0, 0.0};
+    if (stages == 1) *b = b1, *c = c1;
+    else if (stages == 2) *b = b2, *c = c2;
+    else if (stages == 4) *b = b4, *c = c4;
+    else return false;
+    return true;
+}
+
+// Enqueue one step on stream s: every stage's evaluation launched directly
+// (no nested graph) followed by its stage kernel, then the update.
+static int enqueue_step(wke_plan *plan, void *f, double dt, int stages, cudaStream_t s) {
+    const double *b, *c;
+    rk_tableau(stages, &b, &c);
+    const HostPlan &hp = plan->hp;
+    const bool f32 = hp.precision == WKE_FP32;
+    for (int st = 0; st < stages; ++st) {
+        const void *y = st == 0 ? f : plan->rk_y;
+        int e = enqueue(plan, y, plan->rk_k, nullptr, s);
+        if (e) return e;
+        void *ynext = st == stages - 1 ? nullptr : plan->rk_y;
+        e = f32 ? rk_stage_T<float>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s)
+                : rk_stage_T<double>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s);
+        if (e) return e;
+    }
+    return f32 ? rk_final_T<float>(hp, f, plan->rk_acc, dt, s) : rk_final_T<double>(hp, f, plan->rk_acc, dt, s);
+}
+
+// The instantiated graph of a whole step for (f, dt, stages), captured on
+// first use (at most 8 per plan, least recently used evicted).
+static int step_graph_for(wke_plan *p, void *f, double dt, int stages, cudaGraphExec_t *out) {
+    for (StepGraph &g : p->step_graphs)
+        if (g.f == f && g.dt == dt && g.stages == stages) {
+            g.used = ++p->tick;
+            *out = g.exec;
+            return WKE_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(p->s1, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_fail(ce, "step graph capture start");
+    int e = enqueue_step(p, f, dt, stages, p->s1);
+    ce = cudaStreamEndCapture(p->s1, &graph);
+    if (e || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return cuda_fail(e ? (cudaError_t)e : ce, "step graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "step graph instantiation");
+    if (p->step_graphs.size() >= 8) {
+        size_t lru = 0;
+        for (size_t i = 1; i < p->step_graphs.size(); ++i)
+            if (p->step_graphs[i].used < p->step_graphs[lru].used) lru = i;
+        cudaGraphExecDestroy(p->step_graphs[lru].exec);
+        p->step_graphs.erase(p->step_graphs.begin() + lru);
+    }
+    p->step_graphs.push_back({f, dt, stages, exec, ++p->tick});
+    *out = exec;
+    return WKE_OK;
+}
+
 int wke_step(wke_plan *plan, void *f, double dt, int rk_stages) {
     if (!plan || !f) return fail(WKE_ERR_INVALID, "plan and f must be non-NULL");
     if (!std::isfinite(dt)) return fail(WKE_ERR_INVALID, "dt must be finite");
-    // Butcher tableaux: b (weights) and c (nodes of the next stage).
-    static const double b1[1] = {1.0};
-    static const double b2[2] = {0.5, 0.5}, c2[2] = {1.0, 0.0};
-    static const double b4[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, c4[4] = {0.5, 0.5, 1.0, 0.0};
     const double *b, *c;
-    static const double c1[1] = {0.0};
-    if (rk_stages == 1) {
-        b = b1;
-        c = c1;
-    } else if (rk_stages == 2) {
-        b = b2;
-        c = c2;
-    } else if (rk_stages == 4) {
-        b = b4;
-        c = c4;
-    } else {
-        return fail(WKE_ERR_INVALID, "rk_stages must be 1, 2 or 4");
-    }
-    const HostPlan &hp = plan->hp;
+    if (!rk_tableau(rk_stages, &b, &c)) return fail(WKE_ERR_INVALID, "rk_stages must be 1, 2 or 4");
     cudaStream_t s = plan->stream;
-    const bool f32 = hp.precision == WKE_FP32;
-    for (int st = 0; st < rk_stages; ++st) {
-        const void *y = st == 0 ? f : plan->rk_y;
-        int rc = collision(plan, y, plan->rk_k, nullptr, s);
-        if (rc) return rc;
-        const bool last = st == rk_stages - 1;
-        void *ynext = last ? nullptr : plan->rk_y;
-        int e = f32 ? rk_stage_T<float>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s)
-                    : rk_stage_T<double>(hp, f, plan->rk_k, plan->rk_acc, ynext, b[st], c[st] * dt, st == 0, s);
-        if (e) return cuda_fail((cudaError_t)e, "Runge-Kutta stage");
+    int rc;
+    if (plan->dirty && (rc = clear_accumulators(plan, s))) return rc;
+    int e;
+    if (plan->use_graphs && !plan->profiling) {
+        cudaGraphExec_t exec;
+        if ((rc = step_graph_for(plan, f, dt, rk_stages, &exec))) {
+            plan->dirty = true;
+            return rc;
+        }
+        e = (int)cudaGraphLaunch(exec, s);
+    } else {
+        e = enqueue_step(plan, f, dt, rk_stages, s);
     }
-    int e = f32 ? rk_final_T<float>(hp, f, plan->rk_acc, dt, s) : rk_final_T<double>(hp, f, plan->rk_acc, dt, s);
-    if (e) return cuda_fail((cudaError_t)e, "Runge-Kutta update");
+    if (e) {
+        plan->dirty = true;
+        return cuda_fail((cudaError_t)e, "Runge-Kutta step");
+    }
     return WKE_OK;
 }
 

@@ -266,3 +266,45 @@ def test_every_launch_layout_matches_oracle(prec):
         assert rel_max_err(Q, ref) <= TOL[prec]
         with pytest.raises(wke.WkeError):
             wke.wke_plan_set_tuning(plan.handle, 6, 0)
+
+
+def test_step_graph_matches_direct_launches():
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f0 = I.two_gaussians(64, 8.0, 21).astype(np.float32)
+    out = []
+    for graphs in (True, False):
+        with _plan(wke, 2, 64, 8.0, 8, 4, 4, "midpoint", precision="fp32") as plan:
+            wke.wke_plan_use_graphs(plan.handle, graphs)
+            ft = torch.tensor(f0, device="cuda")
+            for _ in range(3):
+                plan.step(ft, 1e-3, 4)
+            torch.cuda.synchronize()
+            out.append(ft.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_workload_2d_n128_rk4_fp32_vs_fp64_and_conservation():
+    """2D N=128, M=512, RK4, dt = 1e-3 (20 of the workload's 200 steps): the
+    FP32 trajectory stays within 1e-5 of the FP64 one, and mass, momentum and
+    energy drift stay small next to their values."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["2d_n128_m512"]
+    f0 = w.initial()
+    finals, moms = {}, {}
+    for prec in ("fp64", "fp32"):
+        with _plan(wke, 2, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+            ft = torch.tensor(f0, dtype=plan.dtype, device="cuda")
+            m0 = plan.moments(ft).cpu().numpy()
+            for _ in range(20):
+                plan.step(ft, 1e-3, 4)
+            m1 = plan.moments(ft).cpu().numpy()
+            torch.cuda.synchronize()
+            finals[prec] = ft.double().cpu().numpy()
+            moms[prec] = (m0, m1)
+    assert rel_max_err(finals["fp32"], finals["fp64"]) <= 1e-5
+    m0, m1 = moms["fp64"]
+    assert abs(m1[0] - m0[0]) <= 1e-6 * abs(m0[0])       # mass
+    assert abs(m1[3] - m0[3]) <= 1e-6 * abs(m0[3])       # energy
+    assert not np.allclose(finals["fp64"], f0)
