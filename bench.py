@@ -365,9 +365,9 @@ SERVE_RATE = 200.0      # mean arrivals per second (Poisson)
 
 def serving_mix():
     """(d, N, n_r, n_s, n_sig) of the mixed stream: 2D N in {64, 128, 256}
-    with M = 4N (N/4 x 4 x 4) and 3D N in {32, 64} with M = 32N (N/2 x 8 x 8);
-    3D N = 48 needs radix-3 transforms, which this build does not have."""
-    return [s for s in I.serving_request_sizes() if not (s[0] == 3 and s[1] == 48)]
+    with M = 4N (N/4 x 4 x 4) and 3D N in {32, 48, 64} with M = 32N
+    (N/2 x 8 x 8)."""
+    return list(I.serving_request_sizes())
 
 
 def _serving_initial(d, N, seed):

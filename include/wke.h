@@ -124,8 +124,8 @@ typedef struct wke_plan_info {
  * NULL. */
 int wke_quadrature_default(wke_quadrature *q);
 
-/* Create a plan for d in {2, 3}, N a power of two (16..256 in 2D, 16..64 in
- * 3D), half-width L > 0, and M = n_r * n_s * n_sig quadrature nodes
+/* Create a plan for d in {2, 3}, N in {16, 32, 48, 64, 96, 128, 256} (2D) or
+ * {16, 32, 48, 64} (3D) (lengths 3 * 2^a use radix-12 stages), half-width L > 0, and M = n_r * n_s * n_sig quadrature nodes
  * (Algorithm 1 inputs: grid size, N_r, N_s, N_sig, nodes and weights).
  * Builds the nodes, weights and shift vectors, the per-axis phase tables
  * exp(-i pi j x / L) and transform twiddles in double precision on the host
@@ -196,7 +196,9 @@ typedef struct wke_tuning {
     int pass2_points_per_thread;   /* axis-0 transform in pass 2: 4 (radices
                                       4,4,4 at N = 64: fewer registers, more
                                       blocks per SM) or 8 (radices 8,8: fewer
-                                      instructions); N >= 128 always uses 8 */
+                                      instructions); N >= 128 always uses 8,
+                                      N = 48, 96 always 12 (get reports the
+                                      value in use; set accepts 12 there) */
     int pass1_units_per_block;     /* units each pass-1 block transforms for its
                                       plane (reuses the plane's coefficients);
                                       0 = automatic */

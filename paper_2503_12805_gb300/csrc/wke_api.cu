@@ -613,20 +613,25 @@ int wke_moments(wke_plan *plan, const void *g, double *out, void *stream) {
     return WKE_OK;
 }
 
+// Pass-2 points per thread the kernels actually use: lengths 3 * 2^a always
+// take 12, N >= 128 always 8, otherwise the tuned value.
+static int effective_p2(const HostPlan &hp) { return hp.N % 3 == 0 ? 12 : hp.N >= 128 ? 8 : hp.tune_p2_points; }
+
 int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out) {
     if (!plan || !out) return fail(WKE_ERR_INVALID, "plan and out must be non-NULL");
-    out->pass2_points_per_thread = plan->hp.N >= 128 ? 8 : plan->hp.tune_p2_points;
+    out->pass2_points_per_thread = effective_p2(plan->hp);
     out->pass1_units_per_block = plan->hp.tune_p1_units_per_block;
     return WKE_OK;
 }
 
 int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
     if (!plan || !t) return fail(WKE_ERR_INVALID, "plan and tuning must be non-NULL");
-    if (t->pass2_points_per_thread != 4 && t->pass2_points_per_thread != 8)
-        return fail(WKE_ERR_INVALID, "pass2_points_per_thread must be 4 or 8");
+    if (t->pass2_points_per_thread != 4 && t->pass2_points_per_thread != 8 &&
+        !(t->pass2_points_per_thread == 12 && plan->hp.N % 3 == 0))
+        return fail(WKE_ERR_INVALID, "pass2_points_per_thread must be 4 or 8 (or 12 for N = 3 * 2^a)");
     if (t->pass1_units_per_block < 0 || t->pass1_units_per_block > chunk_units(plan->hp, plan->hp.groups_per_chunk))
         return fail(WKE_ERR_INVALID, "pass1_units_per_block must be 0..units per chunk");
-    plan->hp.tune_p2_points = t->pass2_points_per_thread;
+    plan->hp.tune_p2_points = t->pass2_points_per_thread == 12 ? 8 : t->pass2_points_per_thread;
     plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
     free_graphs(plan);
     return WKE_OK;
@@ -639,9 +644,10 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     const int p2s[2] = {4, 8};
     const int upc = chunk_units(hp, hp.groups_per_chunk);
     const int p1s[4] = {0, 1, 2, 3};
-    for (int a = 0; a < (hp.N <= 64 ? 2 : 1); ++a)
+    const bool p2_choice = hp.N <= 64 && hp.N % 3 != 0;
+    for (int a = 0; a < (p2_choice ? 2 : 1); ++a)
         for (int b = 0; b < (hp.d == 3 ? 4 : 1); ++b)
-            if (p1s[b] <= upc) cands.push_back(wke_tuning{hp.N >= 128 ? 8 : p2s[a], p1s[b]});
+            if (p1s[b] <= upc) cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b]});
     cudaStream_t s = plan->stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

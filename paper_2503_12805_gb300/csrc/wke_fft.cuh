@@ -1,4 +1,4 @@
-// Device building blocks: complex arithmetic, radix-2/4/8/16 DFTs in
+// Device building blocks: complex arithmetic, radix-2/3/4/8/12/16 DFTs in
 // registers, and a warp-local Stockham line transform.
 //
 // Line transform layout.  A line of N points is held by TPL = N / E threads
@@ -9,6 +9,8 @@
 // per-line shared-memory scratch, padded by one slot per 8 so that the
 // strided stage writes fall into distinct banks; only __syncwarp is needed.
 //
+// Lengths are 2^a (radix-8 or radix-4 stages, then a shorter one) or 3 * 2^a
+// (a radix-12 stage first, then powers of two).
 // Stage s of radix R after radices with product Ns handles butterflies
 // j = t + u * TPL (u < E / R) on inputs x[j + r N / R], twiddles them by
 // w_N^{(j mod Ns) r N / (Ns R)}, applies the R-point DFT and writes output r
@@ -70,6 +72,19 @@ template <typename T, int DIR> struct Dft<T, 4, DIR> {
     }
 };
 
+// 3: X0 = a0 + (a1 + a2), X1,2 = a0 - (a1 + a2) / 2 +- DIR i (sqrt(3) / 2) (a1 - a2).
+template <typename T, int DIR> struct Dft<T, 3, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *a) {
+        const T r3 = (T)0.86602540378443864676;   // sqrt(3) / 2
+        const cx<T> s = cadd<T>(a[1], a[2]);
+        const cx<T> dd = mul_i<T, DIR>(cscale<T>(csub<T>(a[1], a[2]), r3));
+        const cx<T> m = csub<T>(a[0], cscale<T>(s, (T)0.5));
+        a[0] = cadd<T>(a[0], s);
+        a[1] = cadd<T>(m, dd);
+        a[2] = csub<T>(m, dd);
+    }
+};
+
 // 8 = 2 x 4: DFT4 of the even and odd samples, twiddle, radix-2 combine.
 template <typename T, int DIR> struct Dft<T, 8, DIR> {
     __device__ __forceinline__ static void run(cx<T> *a) {
@@ -124,8 +139,46 @@ template <typename T, int DIR> struct Dft<T, 16, DIR> {
     }
 };
 
+// 12 = 3 x 4: X[k1 + 3 k2] = sum_{n2} w12^{n2 k1} w4^{n2 k2} sum_{n1} a[4 n1 + n2] w3^{n1 k1}.
+template <typename T, int DIR> struct Dft<T, 12, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *a) {
+        const T r3 = (T)0.86602540378443864676;   // cos(pi/6)
+        const T h = (T)0.5;                       // sin(pi/6)
+        cx<T> b[4][3];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            b[n2][0] = a[n2];
+            b[n2][1] = a[4 + n2];
+            b[n2][2] = a[8 + n2];
+            Dft<T, 3, DIR>::run(b[n2]);
+        }
+        // twiddles w12^{n2 k1}: exponents 1, 2 (n2 = 1), 2, 4 (n2 = 2), 3, 6 (n2 = 3)
+        b[1][1] = mul_cs<T, DIR>(b[1][1], r3, h);
+        b[1][2] = mul_cs<T, DIR>(b[1][2], h, r3);
+        b[2][1] = mul_cs<T, DIR>(b[2][1], h, r3);
+        b[2][2] = mul_cs<T, DIR>(b[2][2], -h, r3);
+        b[3][1] = mul_i<T, DIR>(b[3][1]);
+        b[3][2] = mkc<T>(-b[3][2].x, -b[3][2].y);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            cx<T> c[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+            Dft<T, 4, DIR>::run(c);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) a[k1 + 3 * k2] = c[k2];
+        }
+    }
+};
+
 // ------------------------------------------------------------ line transform
 __host__ __device__ constexpr int ce_min(int a, int b) { return a < b ? a : b; }
+// Radix of the next stage for `rem` points left and E points per thread:
+// 12 or 3 while a factor 3 remains, then the largest power of two that
+// divides E (capped by rem).
+__host__ __device__ constexpr int pick_radix(int rem, int E) {
+    return (rem % 12 == 0 && E % 12 == 0) ? 12
+           : (rem % 3 == 0 && E % 3 == 0) ? 3
+                                          : ce_min(rem, E & -E);
+}
 
 template <int N> struct LinePad {
     // padded scratch index: one spare slot per 8 points
@@ -154,16 +207,16 @@ template <typename T, int N> struct ColScratch {
 
 template <typename T, int N, int E, int DIR, int NS, class S> struct LineStages {
     static constexpr int TPL = N / E;
-    static constexpr int R = ce_min(N / NS, E);
+    static constexpr int R = pick_radix(N / NS, E);
     static constexpr int B = E / R;              // butterflies per thread
     static constexpr bool LAST = (NS * R == N);
-    static_assert(E % R == 0, "radix must divide the points per thread");
+    static_assert(E % R == 0 && (N / NS) % R == 0, "radix must divide the points per thread and the rest");
 
     __device__ __forceinline__ static void run(cx<T> (&v)[E], int t, const S &scr, const cx<T> *tw) {
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int j = t + u * TPL;
-            const int jm = j & (NS - 1);
+            const int jm = j % NS;
             cx<T> bf[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) bf[r] = v[u + r * B];
@@ -216,9 +269,9 @@ __device__ __forceinline__ void col_fft(cx<T> (&v)[E], int t, cx<T> *scr, int z,
     LineStages<T, N, E, DIR, 1, ColScratch<T, N>>::run(v, t, s, tw);
 }
 
-// Points per thread by precision and length.
+// Points per thread by precision and length: 8, or 12 for lengths 3 * 2^a.
 template <typename T, int N> struct LineCfg {
-    static constexpr int E = 8;
+    static constexpr int E = N % 3 == 0 ? 12 : 8;
     static constexpr int TPL = N / E;
     static constexpr int LPW = 32 / TPL;
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");

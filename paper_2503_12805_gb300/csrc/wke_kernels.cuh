@@ -331,7 +331,7 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     if (u >= (ng + 1) / 2 + ng * PPG) return;   // block-uniform
     V += (size_t)blockIdx.z * units_per_chunk * 3 * NN;
     const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
-    const int mrow = (N - row) & (N - 1);
+    const int mrow = (N - row) % N;
     const cx<T> *S = nslice + (size_t)ax * NN;
     int fa, fb;
     unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
@@ -344,7 +344,7 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int col = t + e * TPL, mcol = (N - col) & (N - 1);
+        const int col = t + e * TPL, mcol = (N - col) % N;
         const cx<T> s0 = S[(size_t)row * N + col], s1 = S[(size_t)mrow * N + mcol];
         const cx<T> ha = herm_half<T>(cmul<T>(s0, cmul<T>(ra, pa[b1 * N + col])),
                                       cmul<T>(s1, cmul<T>(rma, pa[b1 * N + mcol])));
@@ -397,7 +397,7 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int jb = t + e * TPL, mj = (N - jb) & (N - 1);
+        const int jb = t + e * TPL, mj = (N - jb) % N;
         const cx<T> s0 = S[jb], s1 = S[mj];
         const cx<T> ha = herm_half<T>(cmul<T>(s0, cmul<T>(ca, pa[b * N + jb])), cmul<T>(s1, cmul<T>(ca, pa[b * N + mj])));
         cx<T> hb = mkc<T>((T)0, (T)0);
@@ -426,13 +426,17 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
 // accumulator.
 // Points per thread EP: 4 (radices 4, 4, 4 for N = 64; fewer registers, more
 // blocks per SM) or 8 (radices 8, 8; fewer instructions).  The plan's tuning
-// picks one; N >= 128 always uses 8 so a column fits in one warp.
+// picks one; N >= 128 always uses 8, and lengths 3 * 2^a use 12 (radices 12
+// then powers of two).
 template <typename T, int N, int EP> struct Pass2Cfg {
-    static constexpr int E = N >= 128 ? 8 : EP;
+    static constexpr int E = N % 3 == 0 ? 12 : N >= 128 ? 8 : EP;
     static constexpr int TPL = N / E;                    // threads per column
-    static constexpr int THREADS = 256;
+    // 128 threads for 12 double points per thread, so that the two staged
+    // tiles and the scratch fit in shared memory
+    static constexpr int THREADS = (E == 12 && sizeof(T) == 8) ? 128 : 256;
     static constexpr int CB = THREADS / TPL;             // columns per block (at most)
-    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? (E == 4 ? 3 : 2) : (E == 4 ? 2 : 1);
+    static constexpr int MIN_BLOCKS = E == 12 ? 1 : sizeof(T) == 4 ? (E == 4 ? 3 : 2) : (E == 4 ? 2 : 1);
+    static_assert(THREADS % TPL == 0 && TPL % 2 == 0, "threads per column must divide the block and be even");
 };
 
 // Asynchronous global -> shared copy of one complex value (cp.async); the

@@ -128,7 +128,8 @@ template <typename T, int N, int EP, bool IM, bool NYQ>
 static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
     typedef Pass2Cfg<T, N, EP> Cfg;
     const int P = cols_of(hp);
-    const int CB = std::min(Cfg::CB, P);       // columns per block
+    int CB = std::min(Cfg::CB, P);             // columns per block: a power of two dividing P
+    while (P % CB) CB /= 2;
     const size_t smem = (size_t)(N + LinePad<N>::LEN * CB + 2 * N * CB) * sizeof(cx<T>);
     int rc = 0;
     if ((rc = set_smem(k_pass2<T, N, EP, IM, NYQ>, smem))) return rc;
@@ -150,10 +151,14 @@ static int pass2_ne(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, boo
 
 template <typename T, int N>
 static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
-    if constexpr (N <= 64) {
-        if (hp.tune_p2_points == 8) return pass2_ne<T, N, 8>(hp, p, g0, ng, im, s);
+    if constexpr (N % 3 == 0) {
+        return pass2_ne<T, N, 12>(hp, p, g0, ng, im, s);
+    } else {
+        if constexpr (N <= 64) {
+            if (hp.tune_p2_points == 8) return pass2_ne<T, N, 8>(hp, p, g0, ng, im, s);
+        }
+        return pass2_ne<T, N, 4>(hp, p, g0, ng, im, s);
     }
-    return pass2_ne<T, N, 4>(hp, p, g0, ng, im, s);
 }
 
 // ------------------------------------------------------------------ dispatch on N
@@ -161,7 +166,9 @@ template <typename T> int forward_T(const HostPlan &hp, const DevicePtrs &p, cud
     switch (hp.N) {
         case 16: return forward_n<T, 16>(hp, p, s);
         case 32: return forward_n<T, 32>(hp, p, s);
+        case 48: return forward_n<T, 48>(hp, p, s);
         case 64: return forward_n<T, 64>(hp, p, s);
+        case 96: return forward_n<T, 96>(hp, p, s);
         case 128: return forward_n<T, 128>(hp, p, s);
         case 256: return forward_n<T, 256>(hp, p, s);
     }
@@ -172,7 +179,9 @@ template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int g
     switch (hp.N) {
         case 16: return pass1_n<T, 16>(hp, p, g0, ng, s);
         case 32: return pass1_n<T, 32>(hp, p, g0, ng, s);
+        case 48: return pass1_n<T, 48>(hp, p, g0, ng, s);
         case 64: return pass1_n<T, 64>(hp, p, g0, ng, s);
+        case 96: return pass1_n<T, 96>(hp, p, g0, ng, s);
         case 128: return pass1_n<T, 128>(hp, p, g0, ng, s);
         case 256: return pass1_n<T, 256>(hp, p, g0, ng, s);
     }
@@ -183,7 +192,9 @@ template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int
     switch (hp.N) {
         case 16: return nyquist_n<T, 16>(hp, p, chunk0, nchunks, s);
         case 32: return nyquist_n<T, 32>(hp, p, chunk0, nchunks, s);
+        case 48: return nyquist_n<T, 48>(hp, p, chunk0, nchunks, s);
         case 64: return nyquist_n<T, 64>(hp, p, chunk0, nchunks, s);
+        case 96: return nyquist_n<T, 96>(hp, p, chunk0, nchunks, s);
         case 128: return nyquist_n<T, 128>(hp, p, chunk0, nchunks, s);
         case 256: return nyquist_n<T, 256>(hp, p, chunk0, nchunks, s);
     }
@@ -195,7 +206,9 @@ int pass2_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cu
     switch (hp.N) {
         case 16: return pass2_n<T, 16>(hp, p, g0, ng, im, s);
         case 32: return pass2_n<T, 32>(hp, p, g0, ng, im, s);
+        case 48: return pass2_n<T, 48>(hp, p, g0, ng, im, s);
         case 64: return pass2_n<T, 64>(hp, p, g0, ng, im, s);
+        case 96: return pass2_n<T, 96>(hp, p, g0, ng, im, s);
         case 128: return pass2_n<T, 128>(hp, p, g0, ng, im, s);
         case 256: return pass2_n<T, 256>(hp, p, g0, ng, im, s);
     }

@@ -164,7 +164,11 @@ static int sphere_rule(int d, int n, int rule, int param, const double *user,
     return fail(WKE_ERR_INVALID, "unknown sphere rule");
 }
 
-static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+// Lengths the kernels are compiled for.
+static bool compiled_length(int d, int N) {
+    if (d == 3) return N == 16 || N == 32 || N == 48 || N == 64;
+    return N == 16 || N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 256;
+}
 
 int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, HostPlan &hp) {
     if (!quad) return fail(WKE_ERR_INVALID, "quadrature descriptor is NULL");
@@ -182,9 +186,9 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     if (quad->dispersion != WKE_OMEGA_HALF_K2 && quad->dispersion != WKE_OMEGA_K2)
         return fail(WKE_ERR_INVALID, "unknown dispersion");
     if (!(quad->R >= 0.0) || !std::isfinite(quad->R)) return fail(WKE_ERR_INVALID, "R must be >= 0");
-    if (!is_pow2(N) || N < 16 || (d == 2 && N > 256) || (d == 3 && N > 64))
+    if (!compiled_length(d, N))
         return fail(WKE_ERR_UNSUPPORTED,
-                    "kernels are built for N a power of two, 16..256 (2D) or 16..64 (3D)");
+                    "kernels are built for N in {16, 32, 48, 64, 96, 128, 256} (2D) or {16, 32, 48, 64} (3D)");
 
     hp = HostPlan();
     hp.d = d;

@@ -47,7 +47,9 @@ def test_version_and_defaults(wke):
     (2, 32, -1.0, 8, 2, 2, 2, -1),       # bad L
     (2, 32, 8.0, 9, 2, 2, 2, -1),        # M != n_r n_s n_sig
     (2, 33, 8.0, 8, 2, 2, 2, -1),        # odd N
-    (2, 48, 8.0, 8, 2, 2, 2, -4),        # valid N, no kernel built
+    (2, 80, 8.0, 8, 2, 2, 2, -4),        # valid N, no kernel built
+    (2, 24, 8.0, 8, 2, 2, 2, -4),        # 3 * 2^3: no kernel built
+    (3, 96, 8.0, 64, 1, 8, 8, -4),       # 96 is built for 2D only
     (3, 128, 8.0, 64, 1, 8, 8, -4),      # 3D N=128 not built
     (3, 32, 8.0, 2 * 7 * 8, 2, 7, 8, -1),  # no Platonic design with 7 points
 ])

@@ -1,7 +1,10 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-Tolerances (relative max-norm against the oracle's max |Q|): FP64 1e-12,
-FP32 1e-5.  Inputs are the seeded generators of ``wke_inputs``.
+Tolerances (relative max-norm against the oracle's max |Q|): FP64 1e-12;
+FP32 1e-5 on the benchmark workloads, and on the other full-field cases the
+larger of 1e-5 and the bound eps32 log2(N^d) kappa derived from the
+cancellation kappa of the four cubic terms (``gpu_util.fp32_tolerance``).
+Inputs are the seeded generators of ``wke_inputs``.
 """
 import math
 
@@ -10,7 +13,7 @@ import pytest
 
 import wke_inputs as I
 from oracle import wke_oracle as O
-from tests.gpu_util import gpu_collision, rel_max_err, require_cuda
+from tests.gpu_util import fp32_tolerance, gpu_collision, rel_max_err, require_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +42,12 @@ CASES = [
      lambda: I.gaussian_noise(3, 16, 8.0, 12, 0.1)),
     ("3d_n32 icosahedron/dodecahedron", 3, 32, 2, 12, 20, "icosahedron", "dodecahedron",
      lambda: I.ring(3, 32, 8.0)),
+    # lengths 3 * 2^a (radix-12 stages)
+    ("2d_n48", 2, 48, 4, 4, 4, "midpoint", None, lambda: I.two_gaussians(48, 8.0, 13)),
+    ("2d_n96 odd sigma rule", 2, 96, 3, 4, 3, "midpoint", None, lambda: I.gaussian_noise(2, 96, 8.0, 14, 0.2)),
+    ("3d_n48 cube", 3, 48, 2, 8, 8, "cube", None, lambda: I.ring(3, 48, 8.0)),
+    ("3d_n48 non-antipodal sigma", 3, 48, 2, 6, 6, "octahedron", "product:2:3",
+     lambda: I.gaussian_noise(3, 48, 8.0, 15, 0.1)),
 ]
 
 
@@ -50,12 +59,14 @@ def test_full_field_parity(case, prec):
     name, d, N, n_r, n_s, n_sig, sph, sph_sig, gen = case
     L = 8.0
     f = gen()
-    ref = O.collision_fast(f, L, _oracle_quad(d, L, n_r, n_s, n_sig, sph, sph_sig), return_complex=True)
+    quad = _oracle_quad(d, L, n_r, n_s, n_sig, sph, sph_sig)
+    ref = O.collision_fast(f, L, quad, return_complex=True)
     with _plan(wke, d, N, L, n_r, n_s, n_sig, sph, sph_sig, precision=prec) as plan:
         Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
     scale = np.max(np.abs(ref))
-    assert rel_max_err(Q, ref.real, scale) <= TOL[prec], name
-    assert rel_max_err(Qim, ref.imag, scale) <= TOL[prec], name
+    tol = TOL[prec] if prec == "fp64" else fp32_tolerance(f, L, quad)
+    assert rel_max_err(Q, ref.real, scale) <= tol, name
+    assert rel_max_err(Qim, ref.imag, scale) <= tol, name
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

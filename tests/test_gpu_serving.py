@@ -21,6 +21,7 @@ MIX = [
     (3, 16, 8, 8, 8, 5, lambda: I.ring(3, 16, 8.0)),
     (2, 64, 16, 4, 4, 2, lambda: I.gaussian_noise(2, 64, 8.0, 4, 0.05)),
     (3, 32, 8, 8, 8, 1, lambda: I.ring(3, 32, 8.0)),
+    (3, 48, 4, 8, 8, 2, lambda: I.ring(3, 48, 8.0)),
 ]
 
 
