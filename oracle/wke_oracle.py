@@ -26,6 +26,8 @@ Evaluators:
   * ``collision_realspace`` the quadrature of Eq. (2.7) with an analytic f.
   * ``collision_at_points`` ``collision_fast`` at chosen grid points only, by
                            direct evaluation of the truncated series (3.1).
+  * ``collision_dealiased`` the linear-sum (de-aliased) counterpart of
+                           ``collision_fast`` through 2N zero padding.
 
 Readings of the paper where it is silent or ambiguous (all listed in the
 design notes): grid k_i = -L + i 2L/N; coefficients by the rectangle rule
@@ -346,6 +348,65 @@ def collision_fast(f: np.ndarray, L: float, quad: Quadrature, nyquist: str = "ke
         K4 = A * C * F
         acc += W * (K1 - K2 + K3 - K4)
     Q = 2.0 ** (1 - d) * acc
+    if return_complex:
+        return Q
+    return Q.real.copy(), float(np.max(np.abs(Q.imag)))
+
+
+# ----------------------------------------------------------------------------
+# The de-aliased sum: linear index sums through zero-padded transforms
+# ----------------------------------------------------------------------------
+
+
+def pad_coefficients(fhat: np.ndarray, factor: int = 2) -> np.ndarray:
+    """The coefficients of the same truncated series (3.1) on a grid `factor`
+    times finer over the same D_L: every mode j in [-N/2, N/2-1]^d keeps its
+    value, the new modes are zero (DFT positions of each grid)."""
+    d, N = fhat.ndim, fhat.shape[0]
+    idx = np.mod(modes_1d(N), factor * N)
+    out = np.zeros((factor * N,) * d, dtype=np.complex128)
+    out[np.ix_(*([idx] * d))] = fhat
+    return out
+
+
+def truncate_coefficients(ghat: np.ndarray, N: int) -> np.ndarray:
+    """The modes j in [-N/2, N/2-1]^d of a finer grid's coefficients, in the
+    DFT positions of the N grid."""
+    d = ghat.ndim
+    idx = np.mod(modes_1d(N), ghat.shape[0])
+    return ghat[np.ix_(*([idx] * d))].copy()
+
+
+def collision_dealiased(f: np.ndarray, L: float, quad: Quadrature, nyquist: str = "keep",
+                        return_complex: bool = False):
+    """The sum of ``collision_fast`` with the linear index sums l + m + n = j
+    of Eqs. (3.3)-(3.6) instead of the circular ones: the classical padding
+    de-aliasing the paper points to for its fast algorithm (Sec. 3.2 remark).
+
+    The coefficients are padded to a 2N grid over the same D_L; there the
+    fields f_N(k - x) and f_N(k) are evaluated, the products are formed and
+    weighted as in ``collision_fast``, and the fine-grid coefficients of the
+    sum are kept on [-N/2, N/2-1]^d.  Products of three series with modes in
+    [-N/2, N/2-1] have modes in [-3N/2, 3N/2-3], and such a mode can reach a
+    kept mode j modulo 2N only through itself, so the kept coefficients are
+    the linear sums exactly.  Returns (Re Q, max |Im Q|) on the N grid, or the
+    complex Q if ``return_complex``."""
+    d, N = f.ndim, f.shape[0]
+    fhat = _apply_nyquist(FFT(f, L), nyquist)
+    ghat = pad_coefficients(fhat, 2)
+    F = iFFT(ghat, L)
+    acc = np.zeros(ghat.shape, dtype=np.complex128)
+    last_q = None
+    C = None
+    for p1, p2, p3, W, q, a, b in quad.nodes():
+        if last_q is None or (p1, p2) != last_q:
+            C = shifted_field(ghat, L, q)
+            last_q = (p1, p2)
+        A = shifted_field(ghat, L, a)
+        B = shifted_field(ghat, L, b)
+        acc += W * (A * C * B - F * C * B + A * F * B - A * C * F)
+    Khat = truncate_coefficients(FFT(2.0 ** (1 - d) * acc, L), N)
+    Q = iFFT(Khat, L)
     if return_complex:
         return Q
     return Q.real.copy(), float(np.max(np.abs(Q.imag)))

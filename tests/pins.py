@@ -132,6 +132,46 @@ def mass_bandlimited(O, d):
     return float(abs(np.sum(q)) / np.sum(np.abs(q)))
 
 
+def dealiased_vs_linear(O, d, nyquist="keep"):
+    """The padded (de-aliased) evaluation against the classical sums of Eqs.
+    (3.3)-(3.6) with linear index sums l + m + n = j and quadrature weights.
+    The rules are not antipodal, so k' and k2' cannot trade places unseen."""
+    if d == 2:
+        N, quad = 8, O.make_quadrature(2, 4, 4, 3, O.default_R(L), "midpoint")
+    else:
+        N, quad = 4, O.make_quadrature(3, 2, 8, 6, O.default_R(L), "cube", "product:2:3")
+    f = I.gaussian_noise(d, N, L, 99, eps=0.2) * I.gaussian(d, N, L, 1.3)
+    qa = O.collision_dealiased(f, L, quad, nyquist=nyquist, return_complex=True)
+    qd = O.iFFT(O.collision_direct(f, L, quad, wrap=False, nyquist=nyquist, return_hat=True), L)
+    return float(np.max(np.abs(qa - qd)) / np.max(np.abs(qd)))
+
+
+def dealiased_mass(O, d):
+    """|sum_i Q_i| / sum_i |Q_i| of the de-aliased operator for an f that is
+    not band-limited, with the same antipodal rule for qhat and sigma: the
+    linear sums have hat K_0 = 0 (Appendix B), whatever the band of f."""
+    if d == 2:
+        N, quad = 16, O.make_quadrature(2, 5, 6, 6, O.default_R(L), "midpoint")
+    else:
+        N, quad = 8, O.make_quadrature(3, 3, 8, 8, O.default_R(L), "cube")
+    f = I.gaussian_noise(d, N, L, 23, eps=0.4) * I.gaussian(d, N, L, 1.5)
+    q = O.collision_dealiased(f, L, quad, return_complex=True)
+    return float(abs(np.sum(q)) / np.sum(np.abs(q)))
+
+
+def dealiased_vs_aliased_bandlimited(O, d):
+    """For a trigonometric polynomial with |j_c| < N/6 the cubic products have
+    modes in (-N/2, N/2) and wrap on the N grid as little as on the 2N grid,
+    so the circular and the linear sums coincide."""
+    N = 18 if d == 2 else 12
+    quad = O.make_quadrature(d, 3, 6 if d == 2 else 8, 5 if d == 2 else 6, O.default_R(L),
+                             "midpoint" if d == 2 else "cube", None if d == 2 else "product:2:3")
+    f = I.trig_poly(d, L, (N - 1) // 6, 8, 3).on_grid(N)
+    qa = O.collision_dealiased(f, L, quad, return_complex=True)
+    qc = O.collision_fast(f, L, quad, return_complex=True)
+    return float(np.max(np.abs(qa - qc)) / np.max(np.abs(qc)))
+
+
 def naive_dft(O, d):
     """FFT/iFFT against Eq. (3.1) summed term by term."""
     N = 6 if d == 2 else 4

@@ -69,6 +69,15 @@ MUTANTS = [
      "    return np.fft.fftn(g) / float(N ** d) * _alternating_sign(d, N)",
      "    return np.fft.fftn(g) / float(N ** d)",
      pins.naive_dft, 2),
+    ("de-aliased: no padding (circular sums)",
+     "    ghat = pad_coefficients(fhat, 2)", "    ghat = pad_coefficients(fhat, 1)",
+     pins.dealiased_vs_linear, 2),
+    ("de-aliased: padded modes stored at the first N positions",
+     "    idx = np.mod(modes_1d(N), factor * N)", "    idx = np.arange(N)",
+     pins.dealiased_vs_linear, 3),
+    ("de-aliased: truncation keeps the first N positions",
+     "    idx = np.mod(modes_1d(N), ghat.shape[0])", "    idx = np.arange(N)",
+     pins.dealiased_vs_linear, 2),
     ("transposed phase table in the shifted field",
      "    return iFFT(fhat * phase(d, N, L, x), L)",
      "    return iFFT(fhat * np.swapaxes(phase(d, N, L, x), 0, 1), L)",

@@ -118,6 +118,30 @@ def test_mass_identity_bandlimited(d):
     assert pins.mass_bandlimited(O, d) < 1e-13
 
 
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("nyquist", ["keep", "zero"])
+def test_dealiased_equals_linear_sums(d, nyquist):
+    """2N padding gives the linear index sums of Eqs. (3.3)-(3.6) exactly."""
+    assert pins.dealiased_vs_linear(O, d, nyquist) < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dealiased_mass_for_any_band(d):
+    """Appendix B for the linear sums with quadrature weights: the mass of Q
+    vanishes for f that is not band-limited (the circular sums do not)."""
+    assert pins.dealiased_mass(O, d) < 1e-13
+    N, quad = (16, O.make_quadrature(2, 5, 6, 6, O.default_R(L), "midpoint")) if d == 2 else \
+        (8, O.make_quadrature(3, 3, 8, 8, O.default_R(L), "cube"))
+    f = I.gaussian_noise(d, N, L, 23, eps=0.4) * I.gaussian(d, N, L, 1.5)
+    qc = O.collision_fast(f, L, quad, return_complex=True)
+    assert abs(np.sum(qc)) / np.sum(np.abs(qc)) > 1e-3       # the check can tell the two apart
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dealiased_equals_aliased_for_narrow_band(d):
+    assert pins.dealiased_vs_aliased_bandlimited(O, d) < 1e-12
+
+
 def test_mass_appendix_b_linear_exact_weights():
     """Appendix B: the non-fast system (linear sums, exact weights) has
     hat K_0 = 0 for any f."""
