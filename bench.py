@@ -278,6 +278,8 @@ def run_gpu(args, rank, world, pool, workers):
     }
     if args.rk:
         line["time_stepping"] = run_time_stepping(wke, torch, dev)
+    if args.dealias:
+        line["dealiased"] = run_dealiased(wke, torch, dev)
     if args.serve_requests > 0:
         line["serving"] = run_serving(args.serve_requests, I.BASE_SEED + 4 + rank, wke, 40 << 30, 8)
     if rank == 0 and pool is not None:
@@ -296,7 +298,7 @@ def kernel_flops(cls, info):
     executed algorithm needs: 5 n log2 n per complex n-point transform, 16 per
     point for the two phase products and the packing of a unit, 30 per point
     per product).  A unit is two shifted fields packed in one transform."""
-    d, N, G = info.d, info.N, info.groups_per_chunk
+    d, N, G = info.d, info.N_compute, info.groups_per_chunk
     nd = N ** d
     P = nd // N
     ppg = info.products_per_group
@@ -311,6 +313,45 @@ def kernel_flops(cls, info):
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * G * nd
+
+
+# ------------------------------------------------------------------ de-aliased variant
+
+def run_dealiased(wke, torch, dev, reps=20):
+    """3D N=32, M=1024 (16 radial x 8 x 8 cube, Gaussian with 1% noise),
+    Nyquist modes zeroed: evals/s of the circular sums (N-point transforms)
+    and of the de-aliased linear sums (2N = 64 grid), FP32 and FP64, CUDA
+    events per evaluation with L2 flushed before each; and |sum Q| / sum |Q|
+    of each FP64 result (the linear sums conserve mass exactly for this rule)."""
+    w = I.WORKLOADS["3d_n32_m1024"]
+    f0 = w.initial()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {"workload": "3d_n32_m1024, Nyquist zeroed; de-aliased transforms on the 64^3 grid"}
+    for dealias in (False, True):
+        key = "dealiased" if dealias else "circular"
+        res = {}
+        for prec in ("fp32", "fp64"):
+            plan = wke.Plan(3, w.N, w.L, w.n_r, w.n_s, w.n_sig, sphere=w.sphere, precision=prec, nyquist="zero",
+                            dealias=dealias)
+            f = torch.tensor(f0, dtype=plan.dtype, device=dev)
+            Q = torch.empty_like(f)
+            for _ in range(3):
+                plan.collision(f, Q)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for i, (a, b) in enumerate(ev):
+                flush.fill_(i & 0xFF)
+                a.record()
+                plan.collision(f, Q)
+                b.record()
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+            res[f"{prec}_evals_per_s"] = round(1000.0 / ms, 3)
+            if prec == "fp64":
+                q = Q.cpu().numpy()
+                res["mass_rel_fp64"] = float(abs(q.sum()) / abs(q).sum())
+            plan.close()
+        out[key] = res
+    return out
 
 
 # ------------------------------------------------------------------ time stepping
@@ -451,6 +492,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch layout")
     ap.add_argument("--no-rk", dest="rk", action="store_false", help="skip the time-stepping section")
+    ap.add_argument("--no-dealias", dest="dealias", action="store_false",
+                    help="skip the de-aliased-variant section")
     ap.add_argument("--serve-requests", type=int, default=120,
                     help="requests in the serving stream (0: skip serving)")
     ap.add_argument("--fp32-only", action="store_true",

@@ -68,6 +68,16 @@ extern "C" {
 #define WKE_NYQ_KEEP  0   /* modes [-N/2, N/2-1]^d as in Eq. (3.1) (default)  */
 #define WKE_NYQ_ZERO  1   /* zero every mode with a component equal to -N/2   */
 
+/* Index sums of the cubic products (Sec. 3.2).  Circular: the N-point
+ * transforms of Algorithm 1, l + m + n = j (mod N).  De-aliased: the linear
+ * sums l + m + n = j of Eqs. (3.3)-(3.6), computed on a 2N grid over the same
+ * domain (zero padding, the classical de-aliasing of the Sec. 3.2 remark);
+ * needs WKE_NYQ_ZERO (the kept -N/2 modes have no partner on the 2N grid, so
+ * its fields would not be real), costs 2^d times the transform work, and
+ * conserves mass exactly for the same antipodal rule on qhat and sigma. */
+#define WKE_ALIAS_CIRCULAR  0
+#define WKE_DEALIAS_PAD2    1
+
 #define WKE_OMEGA_HALF_K2  0   /* omega = |k|^2/2, the paper's numerics (Sec. 2) */
 #define WKE_OMEGA_K2       1   /* omega = |k|^2: the frequency delta halves Q    */
 
@@ -96,6 +106,8 @@ typedef struct wke_quadrature {
                                 node separately, as Algorithm 1 loops          */
     size_t chunk_bytes;      /* budget for the per-chunk intermediate fields;
                                 0 => 48 MiB (sized to stay resident in L2)     */
+    int alias;               /* WKE_ALIAS_CIRCULAR (default) or
+                                WKE_DEALIAS_PAD2                               */
 } wke_quadrature;
 
 typedef struct wke_plan wke_plan;   /* opaque */
@@ -114,6 +126,7 @@ typedef struct wke_plan_info {
                                     complex transform of n points)            */
     double l2_bytes_per_collision; /* intermediate-field traffic (write + read)*/
     size_t device_bytes;     /* device memory the plan owns                    */
+    int N_compute;           /* grid of the transforms: N, or 2N de-aliased    */
 } wke_plan_info;
 
 /* ------------------------------------------------------------ calls */
@@ -125,7 +138,9 @@ typedef struct wke_plan_info {
 int wke_quadrature_default(wke_quadrature *q);
 
 /* Create a plan for d in {2, 3}, N in {16, 32, 48, 64, 96, 128, 256} (2D) or
- * {16, 32, 48, 64} (3D) (lengths 3 * 2^a use radix-12 stages), half-width L > 0, and M = n_r * n_s * n_sig quadrature nodes
+ * {16, 32, 48, 64} (3D) (lengths 3 * 2^a use radix-12 stages; de-aliased
+ * plans need 2N in that set too), half-width L > 0, and M = n_r * n_s * n_sig
+ * quadrature nodes
  * (Algorithm 1 inputs: grid size, N_r, N_s, N_sig, nodes and weights).
  * Builds the nodes, weights and shift vectors, the per-axis phase tables
  * exp(-i pi j x / L) and transform twiddles in double precision on the host
@@ -133,7 +148,8 @@ int wke_quadrature_default(wke_quadrature *q);
  * device.  *out receives the plan (NULL on failure).
  * Errors: WKE_ERR_INVALID (d, N, L, M or the rule out of range, M !=
  * n_r n_s n_sig, unknown Platonic size, user rule with zero-length
- * direction), WKE_ERR_UNSUPPORTED (valid N without a compiled kernel),
+ * direction, WKE_DEALIAS_PAD2 without WKE_NYQ_ZERO), WKE_ERR_UNSUPPORTED
+ * (valid N without a compiled kernel),
  * WKE_ERR_OOM, WKE_ERR_CUDA. */
 int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad,
                     wke_plan **out);

@@ -656,10 +656,12 @@ def moments(g: np.ndarray, L: float) -> np.ndarray:
 
 
 def rk_step(f: np.ndarray, L: float, quad: Quadrature, dt: float, stages: int,
-            nyquist: str = "keep") -> np.ndarray:
+            nyquist: str = "keep", dealias: bool = False) -> np.ndarray:
     """One explicit Runge-Kutta step of df/dt = Re Q(f) on the grid values:
-    1 = forward Euler, 2 = Heun, 4 = classical RK4 (the paper's integrator)."""
-    Q = lambda g: collision_fast(g, L, quad, nyquist)[0]
+    1 = forward Euler, 2 = Heun, 4 = classical RK4 (the paper's integrator).
+    ``dealias`` steps the linear-sum operator of ``collision_dealiased``."""
+    evaluate = collision_dealiased if dealias else collision_fast
+    Q = lambda g: evaluate(g, L, quad, nyquist)[0]
     if stages == 1:
         return f + dt * Q(f)
     if stages == 2:

@@ -22,6 +22,8 @@ template <typename T> int moments_T(const HostPlan &, const void *, double *, do
 template <typename T>
 int rk_stage_T(const HostPlan &, const void *, const void *, double *, void *, double, double, int, cudaStream_t);
 template <typename T> int rk_final_T(const HostPlan &, void *, const double *, double, cudaStream_t);
+template <typename T> int dealias_prepare_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
+template <typename T> int dealias_finish_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
 
 int moments_partials_count(const HostPlan &) { return 256; }
 
@@ -83,6 +85,10 @@ struct wke_plan {
 namespace {
 
 size_t grid_elems(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
+// points of the caller's grids (f, Q): N_in^d
+size_t grid_in_elems(const HostPlan &hp) {
+    return hp.d == 2 ? (size_t)hp.N_in * hp.N_in : (size_t)hp.N_in * hp.N_in * hp.N_in;
+}
 
 int dev_alloc(wke_plan *p, void **ptr, size_t bytes) {
     *ptr = nullptr;
@@ -174,13 +180,16 @@ template <typename T> int upload_tables(wke_plan *p) {
             }
         }
     std::vector<C> tw(hp.N);
-    std::vector<double2> tw64(hp.N);
+    std::vector<double2> tw64(hp.N_in);
     const double two_pi = 6.28318530717958647692528676655900577;
     for (int k = 0; k < hp.N; ++k) {
         const double th = two_pi * k / hp.N;
+        tw[k].x = (T)std::cos(th);
+        tw[k].y = (T)std::sin(th);
+    }
+    for (int k = 0; k < hp.N_in; ++k) {
+        const double th = two_pi * k / hp.N_in;
         tw64[k] = make_double2(std::cos(th), std::sin(th));
-        tw[k].x = (T)tw64[k].x;
-        tw[k].y = (T)tw64[k].y;
     }
     std::vector<int> pl(2 * hp.products_per_group);
     for (int i = 0; i < hp.products_per_group; ++i) {
@@ -203,6 +212,42 @@ template <typename T> int upload_tables(wke_plan *p) {
     if ((e = cudaMemcpy(const_cast<double *>(p->dp.prod_W), hp.prod_W.data(), hp.prod_W.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "weight upload");
+    if (hp.dealias) {
+        // Per-axis maps between the N_in grid k_i = -L + i 2L/N_in and the 2N
+        // grid k'_i = -L + i 2L/N of the same domain, through the modes
+        // j in [-N_in/2, N_in/2-1] of Eq. (3.1):
+        //   interpolation (N x N_in): f_N(k'_a) = sum_b Kint[a][b] f(k_b), with
+        //     Kint[a][b] = (1/N_in) sum_j exp(i pi j (k'_a - k_b) / L) over the
+        //     modes without j = -N_in/2 (the plan zeroes them);
+        //   projection (N_in x N): Q(k_a) = sum_b Kproj[a][b] Q2(k'_b), with
+        //     Kproj[a][b] = (1/N) sum_j exp(i pi j (k_a - k'_b) / L) over all
+        //     of [-N_in/2, N_in/2-1] (Q keeps its -N_in/2 modes).
+        const int n = hp.N, m = hp.N_in;
+        const double pi = 3.14159265358979323846264338327950288;
+        std::vector<double2> Ki((size_t)n * m), Kp((size_t)m * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < m; ++b) {
+                const double dk = (-hp.L + a * 2.0 * hp.L / n) - (-hp.L + b * 2.0 * hp.L / m);
+                double re = 0.0, im = 0.0, rp = 0.0, ip = 0.0;
+                for (int j = -m / 2; j < m / 2; ++j) {
+                    const double c = std::cos(pi * j * dk / hp.L), sn = std::sin(pi * j * dk / hp.L);
+                    if (j != -m / 2) {
+                        re += c;
+                        im += sn;
+                    }
+                    rp += c;      // projection term of (k_b - k'_a) = -dk: conjugate phase
+                    ip -= sn;
+                }
+                Ki[(size_t)a * m + b] = make_double2(re / m, im / m);
+                Kp[(size_t)b * n + a] = make_double2(rp / n, ip / n);
+            }
+        if ((e = cudaMemcpy(const_cast<void *>(p->dp.Kint), Ki.data(), Ki.size() * sizeof(double2),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "interpolation map upload");
+        if ((e = cudaMemcpy(const_cast<void *>(p->dp.Kproj), Kp.data(), Kp.size() * sizeof(double2),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "projection map upload");
+    }
     return WKE_OK;
 }
 
@@ -234,7 +279,9 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
     if (!e) {
         ProfScope ps(p, s1, 0);
         e = forward_T<T>(hp, dp, s1);
+        if (!e && hp.dealias) e = dealias_prepare_T<T>(hp, dp, s1);   // coefficients and f on the 2N grid
     }
+    if (hp.dealias) dp.f = dp.ffine;     // the products take F = f_N on the 2N grid
     // s3 joins only when it has work (a forked stream must be joined back)
     if (nyq && !e) e = (int)cudaEventRecord(p->ev_fwd, s1);
     if (nyq && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_fwd, 0);
@@ -263,13 +310,13 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         if (!e && nyq) e = (int)cudaStreamWaitEvent(s2, p->ev_nq[buf], 0);
         if (!e) {
             ProfScope ps(p, s2, 2);
-            e = pass2_T<T>(hp, dp, g0, ng, Qim != nullptr, s2);
+            e = pass2_T<T>(hp, dp, g0, ng, Qim != nullptr && !hp.dealias, s2);
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p2[buf], s2);
     }
     if (!e) {
         ProfScope ps(p, s2, 3);
-        e = finalize_T<T>(hp, dp, Q, Qim, s2);
+        e = hp.dealias ? dealias_finish_T<T>(hp, dp, Q, Qim, s2) : finalize_T<T>(hp, dp, Q, Qim, s2);
     }
     if (!e) e = (int)cudaEventRecord(p->ev_join, s2);
     if (!e) e = (int)cudaStreamWaitEvent(origin, p->ev_join, 0);
@@ -398,14 +445,22 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
     ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
     ALLOC(p->dp.phase, nf * hp.d * hp.N * cxb);
     ALLOC(p->dp.tw, hp.N * cxb);
-    ALLOC(p->dp.tw64, hp.N * 16);
+    ALLOC(p->dp.tw64, hp.N_in * 16);
+    if (hp.dealias) {
+        ALLOC(p->dp.ghat_in, grid_in_elems(hp) * cxb);
+        ALLOC(p->dp.ffine, nd * tb);
+        ALLOC(p->dp.map0, nd * 16);
+        ALLOC(p->dp.map1, nd * 16);
+        ALLOC(p->dp.Kint, (size_t)hp.N * hp.N_in * 16);
+        ALLOC(p->dp.Kproj, (size_t)hp.N * hp.N_in * 16);
+    }
     ALLOC(p->dp.prod_local, hp.products_per_group * 2 * sizeof(int));
     ALLOC(p->dp.prod_W, (size_t)hp.n_groups * hp.products_per_group * 8);
-    ALLOC(p->f_stage, nd * tb);
-    ALLOC(p->Q_stage, nd * tb);
-    ALLOC(p->rk_y, nd * tb);
-    ALLOC(p->rk_k, nd * tb);
-    ALLOC(p->rk_acc, nd * 8);
+    ALLOC(p->f_stage, grid_in_elems(hp) * tb);
+    ALLOC(p->Q_stage, grid_in_elems(hp) * tb);
+    ALLOC(p->rk_y, grid_in_elems(hp) * tb);
+    ALLOC(p->rk_k, grid_in_elems(hp) * tb);
+    ALLOC(p->rk_acc, grid_in_elems(hp) * 8);
     ALLOC(p->mom_partials, (size_t)moments_partials_count(hp) * (hp.d + 2) * 8);
 #undef ALLOC
     rc = hp.precision == WKE_FP32 ? upload_tables<float>(p) : upload_tables<double>(p);
@@ -449,7 +504,8 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     if (!plan || !info) return fail(WKE_ERR_INVALID, "plan or info is NULL");
     const HostPlan &hp = plan->hp;
     info->d = hp.d;
-    info->N = hp.N;
+    info->N = hp.N_in;
+    info->N_compute = hp.N;
     info->M = hp.M;
     info->precision = hp.precision;
     info->n_groups = hp.n_groups;
@@ -457,7 +513,8 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     info->products_per_group = hp.products_per_group;
     info->groups_per_chunk = hp.groups_per_chunk;
     info->n_chunks = hp.n_chunks;
-    info->launches_per_collision = 2 + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1;
+    info->launches_per_collision = 2 + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1 +
+                                   (hp.dealias ? 1 + 2 * hp.d : 0);
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
     info->device_bytes = plan->bytes;
@@ -492,7 +549,7 @@ int wke_collision(wke_plan *plan, const void *f, void *Q, void *stream) {
 
 int wke_collision_host(wke_plan *plan, const void *f_host, void *Q_host) {
     if (!plan || !f_host || !Q_host) return fail(WKE_ERR_INVALID, "plan, f_host and Q_host must be non-NULL");
-    const size_t bytes = grid_elems(plan->hp) * (plan->hp.precision == WKE_FP64 ? 8 : 4);
+    const size_t bytes = grid_in_elems(plan->hp) * (plan->hp.precision == WKE_FP64 ? 8 : 4);
     cudaStream_t s = plan->stream;
     cudaError_t e = cudaMemcpyAsync(plan->f_stage, f_host, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");

@@ -18,6 +18,10 @@ int fail(int code, const std::string &msg);
 // precision on the host (Sec. 3.3, Eq. (3.8)).
 struct HostPlan {
     int d = 0, N = 0, M = 0;
+    // N is the grid of the transforms; N_in the grid of f and Q.  They differ
+    // only for de-aliased plans (N = 2 N_in, zero padding).
+    int N_in = 0;
+    bool dealias = false;
     double L = 0, R = 0;
     int n_r = 0, n_s = 0, n_sig = 0;
     int precision = WKE_FP64, nyquist = WKE_NYQ_KEEP, dispersion = WKE_OMEGA_HALF_K2;
@@ -86,7 +90,13 @@ struct DevicePtrs {
     double *Qacc_im;          // groups_per_chunk * N^d partial sums (imag) or null
     const void *phase;        // n_fields * d * N complex T phase tables
     const void *tw;           // N complex T twiddles exp(+2 pi i k / N)
-    const double *tw64;       // N complex double twiddles
+    const double *tw64;       // N_in complex double twiddles (forward transform of f)
+    // de-aliased plans only
+    void *ghat_in;            // N_in^d complex T: coefficients of f on its own grid
+    void *ffine;              // N^d T: f_N on the 2N grid (F in the products)
+    void *map0, *map1;        // N^d complex double each: per-axis map buffers
+    const void *Kint;         // N x N_in complex double: values on the 2N grid from the N_in grid
+    const void *Kproj;        // N_in x N complex double: projection onto modes [-N_in/2, N_in/2-1]
     const int *prod_local;    // products_per_group * 2 ints (fa, fb)
     const double *prod_W;     // n_groups * products_per_group
 };
@@ -100,6 +110,10 @@ int launch_forward(const HostPlan &hp, const DevicePtrs &p, void *stream);
 int launch_pass1(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);
 int launch_pass2(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);
 int launch_finalize(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, void *stream);
+// de-aliased plans: coefficients and f on the 2N grid before the chunks;
+// projection of the 2N-grid sum onto the N_in grid after them
+int launch_dealias_prepare(const HostPlan &hp, const DevicePtrs &p, void *stream);
+int launch_dealias_finish(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, void *stream);
 int launch_moments(const HostPlan &hp, const void *g, double *partials, double *out, void *stream);
 int moments_partials_count(const HostPlan &hp);
 int launch_rk_stage(const HostPlan &hp, const void *f, const void *k, double *kacc, void *ystage,

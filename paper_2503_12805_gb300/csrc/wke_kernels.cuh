@@ -612,6 +612,63 @@ __global__ void k_finalize(double *__restrict__ Qacc, double *__restrict__ Qim, 
     }
 }
 
+// ------------------------------------------------------------------ de-aliasing (2N grid)
+// Coefficients of f on the 2N grid: mode j of [-Nin/2, Nin/2-1]^d keeps its
+// value, the other modes of [-N/2, N/2-1]^d (N = 2 Nin) are zero.  Both
+// arrays in DFT order.
+template <typename T>
+__global__ void k_pad_spectrum(const cx<T> *__restrict__ gin, cx<T> *__restrict__ g, int d, int Nin, int N,
+                               size_t ND) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ND; i += (size_t)gridDim.x * blockDim.x) {
+        size_t rest = i, src = 0, stride = 1;
+        bool inside = true;
+        for (int a = d - 1; a >= 0; --a) {
+            const int pos = (int)(rest % N);
+            rest /= N;
+            const int j = pos < N / 2 ? pos : pos - N;       // signed mode on the 2N grid
+            if (j < -Nin / 2 || j >= Nin / 2) inside = false;
+            src += (size_t)(j < 0 ? j + Nin : j) * stride;  // its position on the Nin grid
+            stride *= Nin;
+        }
+        g[i] = inside ? gin[src] : mkc<T>((T)0, (T)0);
+    }
+}
+
+// One axis of a separable linear map in double: out[a][i][b] =
+// sum_{i'} K[i][i'] in[a][i'][b] for a < A, i < n_out, b < B.  Inputs are
+// real (float or double) or complex (double2); outputs complex (double2) or
+// real parts in `out` and imaginary parts in `out_im` (if not null).
+__device__ __forceinline__ double2 as_cx(float v) { return make_double2((double)v, 0.0); }
+__device__ __forceinline__ double2 as_cx(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double2 as_cx(double2 v) { return v; }
+__device__ __forceinline__ void put_cx(double2 *out, double2 *, size_t i, double2 v) { out[i] = v; }
+template <typename T> __device__ __forceinline__ void put_cx(T *out, T *out_im, size_t i, double2 v) {
+    out[i] = (T)v.x;
+    if (out_im) out_im[i] = (T)v.y;
+}
+
+template <typename TIn, typename TOut>
+__global__ void k_axis_map(const TIn *__restrict__ in, TOut *__restrict__ out, TOut *__restrict__ out_im,
+                           const double2 *__restrict__ K, int n_out, int n_in, size_t A, size_t B) {
+    const size_t total = A * (size_t)n_out * B;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = idx % B, r = idx / B;
+        const int i = (int)(r % n_out);
+        const size_t a = r / n_out;
+        const double2 *Kr = K + (size_t)i * n_in;
+        const TIn *src = in + a * n_in * B + b;
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < n_in; ++k) {
+            const double2 x = as_cx(src[(size_t)k * B]);
+            const double2 w = Kr[k];
+            re += w.x * x.x - w.y * x.y;
+            im += w.x * x.y + w.y * x.x;
+        }
+        put_cx(out, out_im, idx, make_double2(re, im));
+    }
+}
+
 // ------------------------------------------------------------------ moments
 // Per-block partial sums of h^d [g, k g, |k|^2 g] in double; a second
 // single-block kernel adds the partials in block order (deterministic).

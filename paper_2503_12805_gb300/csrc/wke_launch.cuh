@@ -21,6 +21,11 @@ template <typename K> static int set_smem(K kernel, size_t bytes) {
 }
 
 static inline size_t nd_of(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
+// points of f and Q (the N_in grid; the transform grid N is twice as fine
+// in a de-aliased plan)
+static inline size_t nd_in(const HostPlan &hp) {
+    return hp.d == 2 ? (size_t)hp.N_in * hp.N_in : (size_t)hp.N_in * hp.N_in * hp.N_in;
+}
 static inline int cols_of(const HostPlan &hp) { return hp.d == 2 ? hp.N : hp.N * hp.N; }
 
 // Warps of a line kernel that walks `lines` independent lines.
@@ -29,9 +34,12 @@ template <typename T, int N> static int line_warps(int lines) {
 }
 
 // ------------------------------------------------------------------ forward
+// Forward transform of f on its own grid (N = N_in).  A de-aliased plan
+// writes the coefficients to ghat_in; the padding kernel moves them to the
+// 2N grid.
 template <typename T, int N> static int forward_n(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
     typedef LineCfg<double, N> Cfg;
-    const int P = cols_of(hp);
+    const int P = hp.d == 2 ? N : N * N;
     double2 *tmp = static_cast<double2 *>(p.fwd_tmp);
     const double2 *tw = reinterpret_cast<const double2 *>(p.tw64);
     int rc = 0;
@@ -52,9 +60,9 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
     const int warps = line_warps<double, N>(P);
     const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
     if ((rc = set_smem(k_fwd_cols<T, N>, smem))) return rc;
-    const double inv_nd = 1.0 / (double)nd_of(hp);
+    const double inv_nd = 1.0 / (double)nd_in(hp);
     k_fwd_cols<T, N><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(
-        tmp, static_cast<cx<T> *>(p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO,
+        tmp, static_cast<cx<T> *>(hp.dealias ? p.ghat_in : p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO,
         hp.nyquist == WKE_NYQ_KEEP ? static_cast<cx<T> *>(p.nslice) : nullptr);
     return (int)cudaGetLastError();
 }
@@ -163,7 +171,7 @@ static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool
 
 // ------------------------------------------------------------------ dispatch on N
 template <typename T> int forward_T(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
-    switch (hp.N) {
+    switch (hp.N_in) {
         case 16: return forward_n<T, 16>(hp, p, s);
         case 32: return forward_n<T, 32>(hp, p, s);
         case 48: return forward_n<T, 48>(hp, p, s);
@@ -227,8 +235,8 @@ int finalize_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cuda
 
 template <typename T>
 int moments_T(const HostPlan &hp, const void *g, double *partials, double *out, cudaStream_t s) {
-    k_moments<T><<<kMomentBlocks, kMomentThreads, 0, s>>>(static_cast<const T *>(g), hp.d, hp.N, hp.L, partials);
-    const double h = 2.0 * hp.L / hp.N;
+    k_moments<T><<<kMomentBlocks, kMomentThreads, 0, s>>>(static_cast<const T *>(g), hp.d, hp.N_in, hp.L, partials);
+    const double h = 2.0 * hp.L / hp.N_in;
     const double hd = hp.d == 2 ? h * h : h * h * h;
     k_moments_reduce<<<1, 32, 0, s>>>(partials, kMomentBlocks, hp.d + 2, hd, out);
     return (int)cudaGetLastError();
@@ -237,7 +245,7 @@ int moments_T(const HostPlan &hp, const void *g, double *partials, double *out, 
 template <typename T>
 int rk_stage_T(const HostPlan &hp, const void *f, const void *k, double *kacc, void *ystage, double b_s,
                double c_next_dt, int first, cudaStream_t s) {
-    const size_t ND = nd_of(hp);
+    const size_t ND = nd_in(hp);
     const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
     k_rk_stage<T><<<blocks, 256, 0, s>>>(static_cast<const T *>(f), static_cast<const T *>(k), kacc,
                                           static_cast<T *>(ystage), b_s, c_next_dt, first, ND);
@@ -245,13 +253,76 @@ int rk_stage_T(const HostPlan &hp, const void *f, const void *k, double *kacc, v
 }
 
 template <typename T> int rk_final_T(const HostPlan &hp, void *f, const double *kacc, double dt, cudaStream_t s) {
-    const size_t ND = nd_of(hp);
+    const size_t ND = nd_in(hp);
     const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
     k_rk_final<T><<<blocks, 256, 0, s>>>(static_cast<T *>(f), kacc, dt, ND);
     return (int)cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ de-aliasing
+// One axis map per call: `in` viewed as [A][n_in][B], `out` as [A][n_out][B].
+template <typename TIn, typename TOut>
+static int axis_map(const TIn *in, TOut *out, TOut *out_im, const double2 *K, int n_out, int n_in, size_t A, size_t B,
+                    cudaStream_t s) {
+    const size_t total = A * (size_t)n_out * B;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_axis_map<TIn, TOut><<<blocks, 256, 0, s>>>(in, out, out_im, K, n_out, n_in, A, B);
+    return (int)cudaGetLastError();
+}
+
+// Before the chunks: the coefficients on the 2N grid (padding) and
+// F = f_N on the 2N grid, by the per-axis interpolation map applied to f.
+template <typename T> int dealias_prepare_T(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
+    const size_t ND = nd_of(hp);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    k_pad_spectrum<T><<<blocks, 256, 0, s>>>(static_cast<const cx<T> *>(p.ghat_in), static_cast<cx<T> *>(p.ghat), hp.d,
+                                             hp.N_in, hp.N, ND);
+    int rc = (int)cudaGetLastError();
+    const int n = hp.N, m = hp.N_in;
+    const double2 *K = static_cast<const double2 *>(p.Kint);
+    double2 *b0 = static_cast<double2 *>(p.map0), *b1 = static_cast<double2 *>(p.map1);
+    const T *f = static_cast<const T *>(p.f);
+    T *ff = static_cast<T *>(p.ffine);
+    if (hp.d == 2) {
+        if (!rc) rc = axis_map<T, double2>(f, b0, nullptr, K, n, m, 1, m, s);
+        if (!rc) rc = axis_map<double2, T>(b0, ff, nullptr, K, n, m, n, 1, s);
+    } else {
+        if (!rc) rc = axis_map<T, double2>(f, b0, nullptr, K, n, m, 1, (size_t)m * m, s);
+        if (!rc) rc = axis_map<double2, double2>(b0, b1, nullptr, K, n, m, n, m, s);
+        if (!rc) rc = axis_map<double2, T>(b1, ff, nullptr, K, n, m, (size_t)n * n, 1, s);
+    }
+    return rc;
+}
+
+// After the chunks: the weighted sum on the 2N grid (scaled, real: the
+// padded fields of a Nyquist-zeroed f are real) projected onto the modes
+// [-N_in/2, N_in/2-1]^d of the N_in grid; real part to Q, imaginary part
+// (from the unpaired -N_in/2 modes of the projection) to Qim.
+template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cudaStream_t s) {
+    const size_t ND = nd_of(hp);
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
+    double *qf = static_cast<double *>(p.map0);
+    k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, hp.groups_per_chunk, ND, hp.scale, qf, nullptr);
+    int rc = (int)cudaGetLastError();
+    const int n = hp.N, m = hp.N_in;
+    const double2 *K = static_cast<const double2 *>(p.Kproj);
+    double2 *b0 = static_cast<double2 *>(p.map0), *b1 = static_cast<double2 *>(p.map1);
+    T *q = static_cast<T *>(Q), *qi = static_cast<T *>(Qim);
+    if (hp.d == 2) {
+        if (!rc) rc = axis_map<double, double2>(qf, b1, nullptr, K, m, n, 1, n, s);
+        if (!rc) rc = axis_map<double2, T>(b1, q, qi, K, m, n, m, 1, s);
+    } else {
+        if (!rc) rc = axis_map<double, double2>(qf, b1, nullptr, K, m, n, 1, (size_t)n * n, s);
+        if (!rc) rc = axis_map<double2, double2>(b1, b0, nullptr, K, m, n, m, n, s);
+        if (!rc) rc = axis_map<double2, T>(b0, q, qi, K, m, n, (size_t)m * m, 1, s);
+    }
+    return rc;
+}
+
 #define WKE_INSTANTIATE(T)                                                                                   \
+    template int dealias_prepare_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                 \
+    template int dealias_finish_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);  \
     template int forward_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                         \
     template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);                 \
     template int nyquist_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);               \

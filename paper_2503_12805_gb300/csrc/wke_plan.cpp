@@ -186,13 +186,22 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     if (quad->dispersion != WKE_OMEGA_HALF_K2 && quad->dispersion != WKE_OMEGA_K2)
         return fail(WKE_ERR_INVALID, "unknown dispersion");
     if (!(quad->R >= 0.0) || !std::isfinite(quad->R)) return fail(WKE_ERR_INVALID, "R must be >= 0");
-    if (!compiled_length(d, N))
+    if (quad->alias != WKE_ALIAS_CIRCULAR && quad->alias != WKE_DEALIAS_PAD2)
+        return fail(WKE_ERR_INVALID, "alias must be WKE_ALIAS_CIRCULAR or WKE_DEALIAS_PAD2");
+    const bool dealias = quad->alias == WKE_DEALIAS_PAD2;
+    if (dealias && quad->nyquist != WKE_NYQ_ZERO)
+        return fail(WKE_ERR_INVALID, "WKE_DEALIAS_PAD2 needs WKE_NYQ_ZERO: a kept -N/2 mode has no partner on "
+                                     "the 2N grid, so the padded fields would not be real");
+    if (!compiled_length(d, N) || !compiled_length(d, dealias ? 2 * N : N))
         return fail(WKE_ERR_UNSUPPORTED,
-                    "kernels are built for N in {16, 32, 48, 64, 96, 128, 256} (2D) or {16, 32, 48, 64} (3D)");
+                    "kernels are built for N in {16, 32, 48, 64, 96, 128, 256} (2D) or {16, 32, 48, 64} (3D); "
+                    "a de-aliased plan also needs 2N in that set");
 
     hp = HostPlan();
     hp.d = d;
-    hp.N = N;
+    hp.N = dealias ? 2 * N : N;
+    hp.N_in = N;
+    hp.dealias = dealias;
     hp.M = M;
     hp.L = L;
     hp.R = quad->R > 0.0 ? quad->R : 4.0 * L / (3.0 + std::sqrt(2.0));
@@ -325,7 +334,7 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     // Chunks of groups whose intermediate fields fit the byte budget.
     size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
     size_t nd = 1;
-    for (int a = 0; a < d; ++a) nd *= (size_t)N;
+    for (int a = 0; a < d; ++a) nd *= (size_t)hp.N;
     // two groups share one C unit, so a group costs products + 1/2 units
     size_t per_pair = (size_t)(2 * hp.products_per_group + 1) * nd * cxb;
     hp.chunk_bytes = quad->chunk_bytes ? quad->chunk_bytes : (size_t)48 << 20;
@@ -378,8 +387,13 @@ size_t plan_device_bytes(const HostPlan &hp) {
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
     bytes += hp.products_per_group * 2 * sizeof(int);
     bytes += (size_t)hp.n_groups * hp.products_per_group * 8;
-    bytes += 2 * nd * tb;                                               // host-call staging
-    bytes += 2 * nd * tb + nd * 8;                                      // RK stage, k, k-sum
+    size_t nin = 1;
+    for (int a = 0; a < hp.d; ++a) nin *= (size_t)hp.N_in;
+    bytes += 2 * nin * tb;                                              // host-call staging
+    bytes += 2 * nin * tb + nin * 8;                                    // RK stage, k, k-sum
+    if (hp.dealias)                                                     // f and Q on the 2N grid,
+        bytes += nd * tb + 2 * nd * 16 + nin * cxb                      // two map buffers, coarse ghat,
+                 + 2 * (size_t)hp.N * hp.N_in * 16;                     // interpolation / projection
     bytes += (size_t)moments_partials_count(hp) * (hp.d + 2) * 8 + (hp.d + 2) * 8;
     return bytes;
 }
@@ -400,7 +414,15 @@ double plan_flops(const HostPlan &hp) {
     double units = total_units(hp);
     double n_fields = (double)hp.n_groups * hp.fields_per_group;
     double n_prod = (double)hp.n_groups * hp.products_per_group;
-    double fwd = 5.0 * nd * lg;
+    double nin = std::pow((double)hp.N_in, hp.d);
+    double fwd = 5.0 * nin * std::log2(nin);
+    if (hp.dealias) {                                      // per-axis interpolation and projection maps
+        double maps = 0, size = nin;
+        for (int a = 0; a < hp.d; ++a) { size = size / hp.N_in * hp.N; maps += size * hp.N_in * 8.0; }
+        size = nd;
+        for (int a = 0; a < hp.d; ++a) { size = size / hp.N * hp.N_in; maps += size * hp.N * 8.0; }
+        fwd += maps;
+    }
     double inv = units * 5.0 * nd * lg;                    // pass 1 + pass 2 transforms
     double c_units = units - (double)hp.n_groups * hp.products_per_group;
     double c_again = ((double)hp.n_groups - c_units) * 5.0 * nd * std::log2((double)hp.N);  // shared C units, axis 0

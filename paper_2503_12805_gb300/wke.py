@@ -31,6 +31,8 @@ WKE_FP64 = 0
 WKE_FP32 = 1
 WKE_NYQ_KEEP = 0
 WKE_NYQ_ZERO = 1
+WKE_ALIAS_CIRCULAR = 0
+WKE_DEALIAS_PAD2 = 1
 WKE_OMEGA_HALF_K2 = 0
 WKE_OMEGA_K2 = 1
 
@@ -45,7 +47,7 @@ class WkeQuadrature(ctypes.Structure):
         ("user_s", C_DOUBLE_P), ("user_sig", C_DOUBLE_P),
         ("R", ctypes.c_double), ("precision", ctypes.c_int), ("nyquist", ctypes.c_int),
         ("dispersion", ctypes.c_int), ("pair_antipodal", ctypes.c_int),
-        ("chunk_bytes", ctypes.c_size_t),
+        ("chunk_bytes", ctypes.c_size_t), ("alias", ctypes.c_int),
     ]
 
 
@@ -72,7 +74,7 @@ class WkePlanInfo(ctypes.Structure):
         ("products_per_group", ctypes.c_int), ("groups_per_chunk", ctypes.c_int),
         ("n_chunks", ctypes.c_int), ("launches_per_collision", ctypes.c_int),
         ("flops_per_collision", ctypes.c_double), ("l2_bytes_per_collision", ctypes.c_double),
-        ("device_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int),
     ]
 
 
@@ -334,7 +336,8 @@ class Plan:
     def __init__(self, d: int, N: int, L: float, n_r: int, n_s: int, n_sig: int,
                  sphere: str | None = None, sphere_sig: str | None = None, R: float = 0.0,
                  precision: str = "fp64", nyquist: str = "keep", pair_antipodal: bool = True,
-                 chunk_bytes: int = 0, dispersion: str = "half_k2", user_s=None, user_sig=None):
+                 chunk_bytes: int = 0, dispersion: str = "half_k2", user_s=None, user_sig=None,
+                 dealias: bool = False):
         import numpy as np
         q = wke_quadrature_default()
         q.n_r, q.n_s, q.n_sig = n_r, n_s, n_sig
@@ -358,6 +361,7 @@ class Plan:
         q.dispersion = {"half_k2": WKE_OMEGA_HALF_K2, "k2": WKE_OMEGA_K2}[dispersion]
         q.pair_antipodal = int(pair_antipodal)
         q.chunk_bytes = chunk_bytes
+        q.alias = WKE_DEALIAS_PAD2 if dealias else WKE_ALIAS_CIRCULAR
         self.d, self.N, self.L = d, N, L
         self.M = n_r * n_s * n_sig
         self.precision = precision

@@ -82,3 +82,27 @@ def test_footprint_scales_with_precision_and_chunk(wke):
     q.chunk_bytes = 8 << 20
     b32s = wke.wke_plan_footprint_bytes(3, 64, 8.0, 2048, q)
     assert b32s < b32 < b64
+
+
+def test_dealias_argument_checks_and_footprint(wke):
+    """De-aliased plans need the Nyquist modes zeroed and 2N among the compiled
+    lengths; they hold more memory than the circular plan of the same N."""
+    size = ctypes.c_size_t()
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = 4, 4, 4
+    q.alias = wke.WKE_DEALIAS_PAD2
+    lib = wke.lib()
+    assert lib.wke_plan_footprint_bytes(2, 32, 8.0, 64, ctypes.byref(q), ctypes.byref(size)) == wke.WKE_ERR_INVALID
+    assert b"NYQ_ZERO" in lib.wke_last_error_string()
+    q.nyquist = wke.WKE_NYQ_ZERO
+    assert lib.wke_plan_footprint_bytes(2, 256, 8.0, 64, ctypes.byref(q), ctypes.byref(size)) == -4
+    q.n_s, q.n_sig = 8, 8
+    assert lib.wke_plan_footprint_bytes(3, 64, 8.0, 256, ctypes.byref(q), ctypes.byref(size)) == -4
+    q.alias = 7
+    assert lib.wke_plan_footprint_bytes(3, 32, 8.0, 256, ctypes.byref(q), ctypes.byref(size)) == wke.WKE_ERR_INVALID
+    q.alias = wke.WKE_DEALIAS_PAD2
+    q.chunk_bytes = 1 << 20            # one group per chunk: buffers scale with the grid
+    dealiased = wke.wke_plan_footprint_bytes(3, 32, 8.0, 256, q)
+    q.alias = wke.WKE_ALIAS_CIRCULAR
+    circular = wke.wke_plan_footprint_bytes(3, 32, 8.0, 256, q)
+    assert dealiased > 4 * circular
