@@ -34,6 +34,20 @@ template <typename T, int N> __host__ __device__ constexpr size_t scratch_elems_
     return (size_t)LineCfg<T, N>::LPW * LinePad<N>::PITCH;
 }
 
+// Asynchronous global -> shared copy of one complex value (cp.async); the
+// issuing thread later reads the same slot after cp.async.wait_group.
+template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T> *dst, const cx<T> *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void load_twiddles(cx<T> *tw, const cx<T> *tw_g) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
@@ -186,7 +200,8 @@ __device__ __forceinline__ cx<T> packed(cx<T> g, cx<T> ea, cx<T> eb) {
 // rows); the rows go through shared memory; then every column z is
 // transformed along axis 1 by N/8 threads spread over the block, with 32
 // consecutive columns per warp, so the stores to H[unit][j1][y][z] are whole
-// rows.
+// rows.  The axis-1 and axis-2 phase rows of a unit's two fields are copied
+// to shared memory (cp.async) one unit ahead of their use.
 template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
 k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
@@ -198,6 +213,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *work = tw + N;
     cx<T> *scratch = work + N * WP;           // row scratch, then column scratch
+    cx<T> *prow = scratch + N * LinePad<N>::PITCH;   // 2 buffers x (field a, field b) x rows 1, 2
     load_twiddles<T, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
@@ -208,6 +224,18 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     const int uend = min(nunits, ubeg + units_per_block);
     const size_t NN = (size_t)N * N;
     const int j1 = blockIdx.x;
+    // rows 1 and 2 of unit u's phase tables: prow[buf][0, 2N) field a, [2N, 4N) field b
+    auto stage_rows = [&](int u) {
+        int fa, fb;
+        unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+        const cx<T> *pa = phase + (size_t)fa * 3 * N + N;
+        const cx<T> *pb = phase + (size_t)(fb >= 0 ? fb : fa) * 3 * N + N;
+        cx<T> *dst = prow + ((u - ubeg) & 1) * 4 * N;
+        for (int i = threadIdx.x; i < 4 * N; i += blockDim.x)
+            cp_async_cx<T>(dst + i, i < 2 * N ? pa + i : pb + (i - 2 * N));
+        cp_async_commit();
+    };
+    if (ubeg < uend) stage_rows(ubeg);
     const cx<T> *grow = ghat + ((size_t)j1 * N + row) * N;
     cx<T> g[E];
 #pragma unroll
@@ -215,20 +243,23 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     for (int u = ubeg; u < uend; ++u) {
         int fa, fb;
         unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
-        const cx<T> *pa = phase + (size_t)fa * 3 * N;
-        const cx<T> a01 = cmul<T>(pa[j1], pa[N + row]);
+        if (u + 1 < uend) stage_rows(u + 1);   // into the buffer unit u - 1 used
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();                       // unit u's rows, copied by the whole block
+        const cx<T> *ra = prow + ((u - ubeg) & 1) * 4 * N, *rb = ra + 2 * N;
+        const cx<T> a01 = cmul<T>(phase[(size_t)fa * 3 * N + j1], ra[row]);
         cx<T> v[E];
         if (fb >= 0) {
-            const cx<T> *pb = phase + (size_t)fb * 3 * N;
-            const cx<T> b01 = cmul<T>(pb[j1], pb[N + row]);
+            const cx<T> b01 = cmul<T>(phase[(size_t)fb * 3 * N + j1], rb[row]);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j3 = t + e * TPL;
-                v[e] = packed<T>(g[e], cmul<T>(pa[2 * N + j3], a01), cmul<T>(pb[2 * N + j3], b01));
+                v[e] = packed<T>(g[e], cmul<T>(ra[N + j3], a01), cmul<T>(rb[N + j3], b01));
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = cmul<T>(g[e], cmul<T>(pa[2 * N + t + e * TPL], a01));
+            for (int e = 0; e < E; ++e) v[e] = cmul<T>(g[e], cmul<T>(ra[N + t + e * TPL], a01));
         }
         line_fft<T, N, E, +1>(v, t, rscr, tw);
 #pragma unroll
@@ -438,20 +469,6 @@ template <typename T, int N, int EP> struct Pass2Cfg {
     static constexpr int MIN_BLOCKS = E == 12 ? 1 : sizeof(T) == 4 ? (E == 4 ? 3 : 2) : (E == 4 ? 2 : 1);
     static_assert(THREADS % TPL == 0 && TPL % 2 == 0, "threads per column must divide the block and be even");
 };
-
-// Asynchronous global -> shared copy of one complex value (cp.async); the
-// issuing thread later reads the same slot after cp.async.wait_group.
-template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T> *dst, const cx<T> *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (sizeof(cx<T>) == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
-}
 
 // Imaginary parts of the Nyquist contributions of a unit's two fields at
 // point (i1, column): sum_ax (-1)^{i_ax} V_ax(other indices), real-slot field

@@ -79,7 +79,7 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
-            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
+            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH + 8 * N) * sizeof(cx<T>);
             if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
             // enough blocks to fill the GPU several times over
             const int upb = std::min(nunits, hp.tune_p1_units_per_block > 0 ? hp.tune_p1_units_per_block : 3);
