@@ -450,11 +450,9 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
 // TPL = N/E threads spread over the block (thread ty holds points
 // ty + e TPL), so every warp reads and writes 32 consecutive columns of one
 // row.  The block transforms C once and keeps s = C + F and cf = C F; for
-// every product of the group it transforms A, forms X = A s - cf and adds
-// the term -cf A, then transforms B and adds B X, since
-// A B (C + F) - C F (A + B) = B (A s - cf) - cf A.  Only one transformed
-// field is live at a time.  The group's sum goes to that group's double
-// accumulator.
+// every product of the group it transforms the unit holding A and B (two
+// fields packed in one transform) and adds (A B) s - cf (A + B).  The
+// group's sum goes to that group's double accumulator.
 // Points per thread EP: 4 (radices 4, 4, 4 for N = 64; fewer registers, more
 // blocks per SM) or 8 (radices 8, 8; fewer instructions).  The plan's tuning
 // picks one; N >= 128 always uses 8, and lengths 3 * 2^a use 12 (radices 12
@@ -497,7 +495,7 @@ __device__ __forceinline__ cx<T> nyq_pair(const cx<T> *__restrict__ Vu, int d, i
 // field) and b (of the imaginary-slot field):
 //   real-slot field = (Re Z + b) + i a,  imaginary-slot field = (Im Z - a) + i b.
 // Then, keeping s = C + F and cf = C F, each product contributes
-// A B (C + F) - C F (A + B) = B (A s - cf) - cf A, written out in real parts.
+// A B (C + F) - C F (A + B) = (A B) s - cf (A + B), written out in real parts.
 template <typename T, int N, int EP, bool IM, bool NYQ>
 __global__ void __launch_bounds__(Pass2Cfg<T, N, EP>::THREADS, Pass2Cfg<T, N, EP>::MIN_BLOCKS)
 k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
@@ -510,16 +508,29 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
     cx<T> *stage = scratch + LinePad<N>::LEN * CB;   // 2 tiles of N x CB, prefetched
+    // 3D with the Nyquist set kept and a tile inside one row of the trailing
+    // axes: each unit's table entries for the tile are staged with it in one
+    // of 3 slots (a slot is rewritten only after a full transform, with its
+    // barriers, since its last read): V_1(i1, i3) for the tile's columns (each
+    // thread copies what it reads), V_2(i1, i2) of the tile's row (copied by
+    // the threads of column 0) and V_0 of the tile's columns.
+    const bool vstage = NYQ && d == 3 && (N % CB) == 0;
+    const int VSLOT = N * CB + N + CB;
+    cx<T> *vbuf = stage + 2 * N * CB;
     load_twiddles<T, N>(tw, tw_g);
     const int z = threadIdx.x % CB, t = threadIdx.x / CB;
     const int col = blockIdx.x * CB + z;
+    const int i2 = col / N, i3 = col - i2 * N;
     const int gl = blockIdx.y;
     const size_t ND = (size_t)N * P;
     const size_t VS = (size_t)d * (ND / N);   // Nyquist table entries per unit
     const int ncu = (ng + 1) >> 1;
     const cx<T> *Hc = H + (size_t)(gl >> 1) * ND;                       // this group's C unit
     const cx<T> *Hp = H + (size_t)(ncu + gl * PPG) * ND;               // its product units
+    const cx<T> *Vc = Vtab + (size_t)(gl >> 1) * VS;
+    const cx<T> *Vp = Vtab + (size_t)(ncu + gl * PPG) * VS;
     const T sgn1 = (t & 1) ? (T)-1 : (T)1;    // (-1)^{i1}: TPL is even, so i1 = t + e TPL has t's parity
+    const T sg2 = (i2 & 1) ? (T)-1 : (T)1, sg3 = (i3 & 1) ? (T)-1 : (T)1;
     const int tiles = 1 + PPG;
     auto prefetch = [&](int k) {
         const cx<T> *src = k == 0 ? Hc : Hp + (size_t)(k - 1) * ND;
@@ -527,7 +538,26 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
 #pragma unroll
         for (int e = 0; e < E; ++e)
             cp_async_cx<T>(dst + (t + e * TPL) * CB + z, src + (size_t)(t + e * TPL) * P + col);
+        if (vstage) {
+            const cx<T> *vs = k == 0 ? Vc : Vp + (size_t)(k - 1) * VS;
+            cx<T> *vd = vbuf + (k % 3) * VSLOT;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                cp_async_cx<T>(vd + (t + e * TPL) * CB + z, vs + N * N + (t + e * TPL) * N + i3);
+            if (z == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) cp_async_cx<T>(vd + N * CB + t + e * TPL, vs + 2 * N * N + (t + e * TPL) * N + i2);
+            }
+            if (t == 0) cp_async_cx<T>(vd + N * CB + N + z, vs + col);
+        }
         cp_async_commit();
+    };
+    // Nyquist imaginary parts of tile k's unit at (i1, this column) from the
+    // staged slot (same sum as nyq_pair)
+    auto nyq_staged = [&](int k, int i1) -> cx<T> {
+        const cx<T> *vd = vbuf + (k % 3) * VSLOT;
+        const cx<T> v0 = vd[N * CB + N + z], v1 = vd[i1 * CB + z], v2 = vd[N * CB + i1];
+        return mkc<T>(sgn1 * v0.x + sg2 * v1.x + sg3 * v2.x, sgn1 * v0.y + sg2 * v1.y + sg3 * v2.y);
     };
     auto take = [&](int k, cx<T> (&v)[E]) {
         const cx<T> *src = stage + (k & 1) * N * CB;
@@ -546,13 +576,12 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
     {
         const bool odd = gl & 1;
         const bool has_partner = (gl ^ 1) < ng;
-        const cx<T> *Vc = Vtab + (size_t)(gl >> 1) * VS;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i1 = t + e * TPL;
             T re = odd ? v[e].y : v[e].x, im = (T)0;
             if (NYQ) {
-                const cx<T> ab = nyq_pair<T, N>(Vc, d, i1, col, sgn1);
+                const cx<T> ab = vstage ? nyq_staged(0, i1) : nyq_pair<T, N>(Vc, d, i1, col, sgn1);
                 const T self = odd ? ab.y : ab.x, part = has_partner ? (odd ? ab.x : ab.y) : (T)0;
                 re += odd ? -part : part;
                 im = self;
@@ -571,7 +600,6 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
         ai[e] = (T)0;
     }
     const double *Wg = prod_W + (size_t)(g0 + gl) * PPG;
-    const cx<T> *Vp = Vtab + (size_t)(ncu + gl * PPG) * VS;
     for (int p = 0; p < PPG; ++p) {
         const T W = (T)Wg[p];
         if (p + 2 < tiles) prefetch(p + 2);   // buffer of tile p, already read
@@ -584,15 +612,15 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
             const int i1 = t + e * TPL;
             T a = (T)0, b = (T)0;
             if (NYQ) {
-                const cx<T> ab = nyq_pair<T, N>(Vp + (size_t)p * VS, d, i1, col, sgn1);
+                const cx<T> ab = vstage ? nyq_staged(p + 1, i1) : nyq_pair<T, N>(Vp + (size_t)p * VS, d, i1, col, sgn1);
                 a = ab.x;
                 b = ab.y;
             }
             const T Ar = v[e].x + b, Br = v[e].y - a;          // A = Ar + i a, B = Br + i b
-            const T xr = Ar * sr[e] - a * si[e] - cr[e];       // X = A s - cf
-            const T xi = Ar * si[e] + a * sr[e] - ci[e];
-            ar[e] += W * (Br * xr - b * xi - (cr[e] * Ar - ci[e] * a));
-            if (IM) ai[e] += W * (Br * xi + b * xr - (cr[e] * a + ci[e] * Ar));
+            const T pr = Ar * Br - a * b, pim = Ar * b + a * Br;   // A B
+            const T ur = Ar + Br, ui = a + b;                  // A + B
+            ar[e] += W * ((pr * sr[e] - pim * si[e]) - (cr[e] * ur - ci[e] * ui));
+            if (IM) ai[e] += W * ((pr * si[e] + pim * sr[e]) - (cr[e] * ui + ci[e] * ur));
         }
     }
     cp_async_wait<0>();

@@ -138,7 +138,10 @@ static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cu
     const int P = cols_of(hp);
     int CB = std::min(Cfg::CB, P);             // columns per block: a power of two dividing P
     while (P % CB) CB /= 2;
-    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB + 2 * N * CB) * sizeof(cx<T>);
+    // two stage buffers for unit tiles, and with the Nyquist set kept in 3D
+    // three slots of staged table entries
+    const size_t vslots = NYQ && hp.d == 3 && N % CB == 0 ? (size_t)3 * (N * CB + N + CB) : 0;
+    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB + 2 * N * CB + vslots) * sizeof(cx<T>);
     int rc = 0;
     if ((rc = set_smem(k_pass2<T, N, EP, IM, NYQ>, smem))) return rc;
     dim3 grid(P / CB, ng);
