@@ -102,8 +102,12 @@ typedef struct wke_quadrature {
     int pair_antipodal;      /* 1 (default): when the sigma rule is antipodal
                                 with equal weights, evaluate the identical
                                 fields f_N(k - b(sigma)) = f_N(k - a(-sigma))
-                                and the identical node products once; 0: every
-                                node separately, as Algorithm 1 loops          */
+                                and the identical node products once, and
+                                skip the nodes with sigma = +-qhat, whose
+                                bracket is identically zero when F = f_N on
+                                the transform grid (Nyquist kept, or
+                                de-aliased); 0: every node separately, as
+                                Algorithm 1 loops                              */
     size_t chunk_bytes;      /* budget for the per-chunk intermediate fields;
                                 0 => 48 MiB (sized to stay resident in L2)     */
     int alias;               /* WKE_ALIAS_CIRCULAR (default) or

@@ -191,8 +191,8 @@ template <typename T> int upload_tables(wke_plan *p) {
         const double th = two_pi * k / hp.N_in;
         tw64[k] = make_double2(std::cos(th), std::sin(th));
     }
-    std::vector<int> pl(2 * hp.products_per_group);
-    for (int i = 0; i < hp.products_per_group; ++i) {
+    std::vector<int> pl(2 * hp.prod_fa.size());
+    for (size_t i = 0; i < hp.prod_fa.size(); ++i) {
         pl[2 * i] = hp.prod_fa[i];
         pl[2 * i + 1] = hp.prod_fb[i];
     }
@@ -454,7 +454,7 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         ALLOC(p->dp.Kint, (size_t)hp.N * hp.N_in * 16);
         ALLOC(p->dp.Kproj, (size_t)hp.N * hp.N_in * 16);
     }
-    ALLOC(p->dp.prod_local, hp.products_per_group * 2 * sizeof(int));
+    ALLOC(p->dp.prod_local, hp.prod_fa.size() * 2 * sizeof(int));
     ALLOC(p->dp.prod_W, (size_t)hp.n_groups * hp.products_per_group * 8);
     ALLOC(p->f_stage, grid_in_elems(hp) * tb);
     ALLOC(p->Q_stage, grid_in_elems(hp) * tb);

@@ -42,7 +42,7 @@ struct HostPlan {
     std::vector<int> anti;               // sigma index of -sigma (paired only)
     int fields_per_group = 0, products_per_group = 0, n_groups = 0;
     std::vector<double> field_shift;     // n_groups * fields_per_group * d
-    std::vector<int> prod_fa, prod_fb;   // products_per_group local field ids
+    std::vector<int> prod_fa, prod_fb;   // n_groups * products_per_group local field ids
     std::vector<double> prod_W;          // n_groups * products_per_group weights
 
     // Chunking of groups through the intermediate buffer.  Pass 1 transforms
@@ -97,7 +97,7 @@ struct DevicePtrs {
     void *map0, *map1;        // N^d complex double each: per-axis map buffers
     const void *Kint;         // N x N_in complex double: values on the 2N grid from the N_in grid
     const void *Kproj;        // N_in x N complex double: projection onto modes [-N_in/2, N_in/2-1]
-    const int *prod_local;    // products_per_group * 2 ints (fa, fb)
+    const int *prod_local;    // n_groups * products_per_group * 2 ints: local fields (fa, fb)
     const double *prod_W;     // n_groups * products_per_group
 };
 

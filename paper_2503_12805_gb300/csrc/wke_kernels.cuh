@@ -181,8 +181,9 @@ __device__ __forceinline__ void unit_fields(int u, int g0, int ng, int FPG, int 
     } else {
         const int k = u - ncu;
         const int gl = k / PPG, p = k - gl * PPG;
-        fa = (g0 + gl) * FPG + prod_local[2 * p];
-        fb = (g0 + gl) * FPG + prod_local[2 * p + 1];
+        const int slot = (g0 + gl) * PPG + p;
+        fa = (g0 + gl) * FPG + prod_local[2 * slot];
+        fb = (g0 + gl) * FPG + prod_local[2 * slot + 1];
     }
 }
 

@@ -286,26 +286,57 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
         }
     }
 
-    // Field and product layout per group.
+    // Field and product layout per group.  With pairing, local field 1 + i
+    // is f_N(k - a_i); the product of the pair (i, anti(i)) takes fields
+    // 1 + i and 1 + anti(i).  Without it, fields 1 + 2i and 2 + 2i are A_i and B_i.
     hp.n_groups = hp.n_r * hp.n_s;
+    std::vector<int> base_fa, base_fb, base_node;     // base products: local fields, first sigma index
     if (hp.paired) {
         hp.fields_per_group = 1 + hp.n_sig;
-        hp.products_per_group = hp.n_sig / 2;
         for (int i = 0; i < hp.n_sig; ++i)
             if (hp.anti[i] > i) {
-                hp.prod_fa.push_back(1 + i);
-                hp.prod_fb.push_back(1 + hp.anti[i]);
+                base_fa.push_back(1 + i);
+                base_fb.push_back(1 + hp.anti[i]);
+                base_node.push_back(i);
             }
     } else {
         hp.fields_per_group = 1 + 2 * hp.n_sig;
-        hp.products_per_group = hp.n_sig;
         for (int i = 0; i < hp.n_sig; ++i) {
-            hp.prod_fa.push_back(1 + 2 * i);
-            hp.prod_fb.push_back(2 + 2 * i);
+            base_fa.push_back(1 + 2 * i);
+            base_fb.push_back(2 + 2 * i);
+            base_node.push_back(i);
         }
     }
+    // Vanishing nodes.  For sigma = qhat, k' = k and k2' = k - q (a = 0,
+    // b = q); for sigma = -qhat the two swap.  Then A = F and B = C (or the
+    // reverse) and A B (C + F) - C F (A + B) = 0 identically, provided F is
+    // the interpolant's value f_N(k): true on the grid when the Nyquist modes
+    // are kept, and on the 2N grid of a de-aliased plan; not with the modes
+    // zeroed on the N grid, where F = f(k) differs from f_N(k).  With pairing
+    // on, such products are dropped (an exact simplification, like the
+    // pairing); without it every node is evaluated as Algorithm 1 loops.
+    const bool drop = hp.paired && (hp.nyquist == WKE_NYQ_KEEP || hp.dealias);
+    std::vector<std::vector<int>> keep(hp.n_groups);
+    size_t ppg = 0;
+    for (int g = 0; g < hp.n_groups; ++g) {
+        const int p2 = g % hp.n_s;
+        for (size_t k = 0; k < base_fa.size(); ++k) {
+            const int i = base_node[k];
+            double dp = 0.0, dm = 0.0;
+            for (int a = 0; a < d; ++a) {
+                dp = std::max(dp, std::fabs(hp.sig[i * d + a] - hp.qhat[p2 * d + a]));
+                dm = std::max(dm, std::fabs(hp.sig[i * d + a] + hp.qhat[p2 * d + a]));
+            }
+            if (!(drop && (dp < 1e-13 || dm < 1e-13))) keep[g].push_back((int)k);
+        }
+        ppg = std::max(ppg, keep[g].size());
+    }
+    // a uniform count per group (groups with fewer get zero-weight padding)
+    hp.products_per_group = (int)std::max<size_t>(1, ppg);
     hp.field_shift.assign((size_t)hp.n_groups * hp.fields_per_group * d, 0.0);
     hp.prod_W.assign((size_t)hp.n_groups * hp.products_per_group, 0.0);
+    hp.prod_fa.assign((size_t)hp.n_groups * hp.products_per_group, base_fa[0]);
+    hp.prod_fb.assign((size_t)hp.n_groups * hp.products_per_group, base_fb[0]);
     for (int g = 0; g < hp.n_groups; ++g) {
         int node0 = g * hp.n_sig;
         double *fs = &hp.field_shift[(size_t)g * hp.fields_per_group * d];
@@ -321,13 +352,12 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
                 }
             }
         }
-        if (hp.paired) {
-            int k = 0;
-            for (int i = 0; i < hp.n_sig; ++i)
-                if (hp.anti[i] > i)
-                    hp.prod_W[(size_t)g * hp.products_per_group + k++] = hp.W[node0 + i] + hp.W[node0 + hp.anti[i]];
-        } else {
-            for (int i = 0; i < hp.n_sig; ++i) hp.prod_W[(size_t)g * hp.products_per_group + i] = hp.W[node0 + i];
+        for (size_t j = 0; j < keep[g].size(); ++j) {
+            const int k = keep[g][j], i = base_node[k];
+            const size_t slot = (size_t)g * hp.products_per_group + j;
+            hp.prod_fa[slot] = base_fa[k];
+            hp.prod_fb[slot] = base_fb[k];
+            hp.prod_W[slot] = hp.paired ? hp.W[node0 + i] + hp.W[node0 + hp.anti[i]] : hp.W[node0 + i];
         }
     }
 
@@ -385,7 +415,7 @@ size_t plan_device_bytes(const HostPlan &hp) {
     bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
     bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
-    bytes += hp.products_per_group * 2 * sizeof(int);
+    bytes += (size_t)hp.n_groups * hp.products_per_group * 2 * sizeof(int);
     bytes += (size_t)hp.n_groups * hp.products_per_group * 8;
     size_t nin = 1;
     for (int a = 0; a < hp.d; ++a) nin *= (size_t)hp.N_in;

@@ -166,9 +166,35 @@ def test_pairing_and_chunking_do_not_change_the_sum():
         with _plan(wke, 3, 32, 8.0, 5, 8, 8, "cube", pair_antipodal=pair, chunk_bytes=chunk) as plan:
             info = plan.info()
             assert info.fields_per_group == (9 if pair else 17)
+            assert info.products_per_group == (3 if pair else 8)
             res.append(gpu_collision(torch, plan, f))
     for r in res[1:]:
         assert rel_max_err(r, res[0]) <= 1e-13
+
+
+def test_vanishing_nodes_dropped_only_where_exactly_zero():
+    """sigma = +-qhat makes {k', k2'} = {k, k - q}: the bracket vanishes when
+    F equals the interpolant on the transform grid.  The cube rule pairs into
+    4 products per group, one of them (qhat, -qhat); it is dropped with the
+    Nyquist modes kept and in a de-aliased plan, kept when F = f(k) differs
+    from the zeroed interpolant, and every node stays without pairing."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.gaussian_noise(3, 16, 8.0, 43, 0.1)
+    quad = _oracle_quad(3, 8.0, 2, 8, 8, "cube")
+    for kw, ppg, oracle in (
+            (dict(), 3, lambda: O.collision_fast(f, 8.0, quad, return_complex=True)),
+            (dict(nyquist="zero"), 4, lambda: O.collision_fast(f, 8.0, quad, nyquist="zero", return_complex=True)),
+            (dict(nyquist="zero", dealias=True), 3,
+             lambda: O.collision_dealiased(f, 8.0, quad, nyquist="zero", return_complex=True)),
+            (dict(pair_antipodal=False), 8, lambda: O.collision_fast(f, 8.0, quad, return_complex=True))):
+        with _plan(wke, 3, 16, 8.0, 2, 8, 8, "cube", **kw) as plan:
+            assert plan.info().products_per_group == ppg, kw
+            Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
+        ref = oracle()
+        scale = np.max(np.abs(ref))
+        assert rel_max_err(Q, ref.real, scale) <= 1e-12, kw
+        assert rel_max_err(Qim, ref.imag, scale) <= 1e-12, kw
 
 
 def test_deterministic_repeat():
