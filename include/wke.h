@@ -78,6 +78,17 @@ extern "C" {
 #define WKE_ALIAS_CIRCULAR  0
 #define WKE_DEALIAS_PAD2    1
 
+/* Evaluation layout (results agree to rounding).  Per group: each
+ * quadrature group (radius, direction) transforms its own C and product
+ * fields and pass 2 forms the products as it transforms them.  Shared: a
+ * chunk of groups transforms each distinct shifted field once (with
+ * symmetric rules many coincide: 26 instead of 56 per radius for the cube
+ * rule), then a product pass reads them.  Auto picks shared when it saves
+ * at least 15% of the transforms. */
+#define WKE_LAYOUT_AUTO       0
+#define WKE_LAYOUT_PER_GROUP  1
+#define WKE_LAYOUT_SHARED     2
+
 #define WKE_OMEGA_HALF_K2  0   /* omega = |k|^2/2, the paper's numerics (Sec. 2) */
 #define WKE_OMEGA_K2       1   /* omega = |k|^2: the frequency delta halves Q    */
 
@@ -112,6 +123,8 @@ typedef struct wke_quadrature {
                                 0 => 48 MiB (sized to stay resident in L2)     */
     int alias;               /* WKE_ALIAS_CIRCULAR (default) or
                                 WKE_DEALIAS_PAD2                               */
+    int layout;              /* WKE_LAYOUT_AUTO (default), _PER_GROUP or
+                                _SHARED                                        */
 } wke_quadrature;
 
 typedef struct wke_plan wke_plan;   /* opaque */
@@ -131,6 +144,9 @@ typedef struct wke_plan_info {
     double l2_bytes_per_collision; /* intermediate-field traffic (write + read)*/
     size_t device_bytes;     /* device memory the plan owns                    */
     int N_compute;           /* grid of the transforms: N, or 2N de-aliased    */
+    int shared_fields;       /* 1 when the plan uses WKE_LAYOUT_SHARED         */
+    int units_per_collision; /* packed transforms (two fields each) per
+                                evaluation                                     */
 } wke_plan_info;
 
 /* ------------------------------------------------------------ calls */
@@ -250,11 +266,13 @@ int wke_plan_use_graphs(wke_plan *plan, int enable);
  * wke_plan_profile_read() must be called after that stream is idle: it adds
  * up the recorded intervals per kernel class into out_host[2 * WKE_PROF_CLASSES]
  * as (total milliseconds, number of launches) pairs, in the order forward,
- * pass 1, pass 2, finalize, Nyquist tables, and forgets them.  Enabling resets the record.
+ * pass 1, pass 2 (the product pass in the shared-field layout), finalize,
+ * Nyquist tables, axis-0 transform (shared-field layout), and forgets them.
+ * Enabling resets the record.
  * While enabled, evaluations launch directly (no graph replay) and the two
  * passes of consecutive chunks do not overlap, so each interval is one
  * kernel's own duration. */
-#define WKE_PROF_CLASSES 5
+#define WKE_PROF_CLASSES 6
 int wke_plan_profile(wke_plan *plan, int enable);
 int wke_plan_profile_read(wke_plan *plan, double *out_host);
 

@@ -14,15 +14,17 @@ namespace wke {
 const char *last_error();
 
 template <typename T> int forward_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
-template <typename T> int pass1_T(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);
-template <typename T> int nyquist_T(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);
-template <typename T> int pass2_T(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);
+template <typename T> int pass1_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
+template <typename T> int nyquist_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
+template <typename T> int pass2_T(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
 template <typename T> int finalize_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
 template <typename T> int moments_T(const HostPlan &, const void *, double *, double *, cudaStream_t);
 template <typename T>
 int rk_stage_T(const HostPlan &, const void *, const void *, double *, void *, double, double, int, cudaStream_t);
 template <typename T> int rk_final_T(const HostPlan &, void *, const double *, double, cudaStream_t);
 template <typename T> int dealias_prepare_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
+template <typename T> int axis0_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
+template <typename T> int products_T(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
 template <typename T> int dealias_finish_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
 
 int moments_partials_count(const HostPlan &) { return 256; }
@@ -166,7 +168,7 @@ struct ProfScope {
 template <typename T> int upload_tables(wke_plan *p) {
     const HostPlan &hp = p->hp;
     typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type C;
-    const int nf = hp.n_groups * hp.fields_per_group;
+    const int nf = hp.n_fields_total;
     std::vector<C> phase((size_t)nf * hp.d * hp.N);
     std::vector<double> row(2 * hp.N);
     for (int f = 0; f < nf; ++f)
@@ -212,6 +214,12 @@ template <typename T> int upload_tables(wke_plan *p) {
     if ((e = cudaMemcpy(const_cast<double *>(p->dp.prod_W), hp.prod_W.data(), hp.prod_W.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "weight upload");
+    if (hp.shared) {
+        std::vector<int> gc(hp.group_cfield);
+        if ((e = cudaMemcpy(const_cast<int *>(p->dp.group_cfield), gc.data(), gc.size() * sizeof(int),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "group table upload");
+    }
     if (hp.dealias) {
         // Per-axis maps between the N_in grid k_i = -L + i 2L/N_in and the 2N
         // grid k'_i = -L + i 2L/N of the same domain, through the modes
@@ -252,7 +260,7 @@ template <typename T> int upload_tables(wke_plan *p) {
 }
 
 int clear_accumulators(wke_plan *p, cudaStream_t s) {
-    const size_t acc = (size_t)p->hp.groups_per_chunk * grid_elems(p->hp) * sizeof(double);
+    const size_t acc = (size_t)n_accumulators(p->hp) * grid_elems(p->hp) * sizeof(double);
     cudaError_t e = cudaMemsetAsync(p->dp.Qacc, 0, acc, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->dp.Qacc_im, 0, acc, s);
     if (e != cudaSuccess) return cuda_fail(e, "accumulator reset");
@@ -285,9 +293,8 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
     // s3 joins only when it has work (a forked stream must be joined back)
     if (nyq && !e) e = (int)cudaEventRecord(p->ev_fwd, s1);
     if (nyq && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_fwd, 0);
+    const bool im = Qim != nullptr && !hp.dealias;
     for (int c = 0; c < hp.n_chunks && !e; ++c) {
-        const int g0 = c * hp.groups_per_chunk;
-        const int ng = std::min(hp.groups_per_chunk, hp.n_groups - g0);
         const int buf = c & 1;
         dp.H = p->Hbuf[buf];
         dp.V = p->Vbuf[buf];
@@ -296,21 +303,25 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
             if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_p2[buf], 0);
             if (!e) {
                 ProfScope ps(p, s3, 4);
-                e = nyquist_T<T>(hp, dp, c, 1, s3);
+                e = nyquist_T<T>(hp, dp, c, s3);
             }
             if (!e) e = (int)cudaEventRecord(p->ev_nq[buf], s3);
         }
         if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
         if (!e) {
             ProfScope ps(p, s1, 1);
-            e = pass1_T<T>(hp, dp, g0, ng, s1);
+            e = pass1_T<T>(hp, dp, c, s1);
+        }
+        if (hp.shared && !e) {            // shared-field layout: axis 0 in place, then the product pass
+            ProfScope ps(p, s1, 5);
+            e = axis0_T<T>(hp, dp, c, s1);
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p1[buf], s1);
         if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_p1[buf], 0);
         if (!e && nyq) e = (int)cudaStreamWaitEvent(s2, p->ev_nq[buf], 0);
         if (!e) {
             ProfScope ps(p, s2, 2);
-            e = pass2_T<T>(hp, dp, g0, ng, Qim != nullptr && !hp.dealias, s2);
+            e = hp.shared ? products_T<T>(hp, dp, c, im, s2) : pass2_T<T>(hp, dp, c, im, s2);
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p2[buf], s2);
     }
@@ -425,7 +436,7 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
     const HostPlan &hp = p->hp;
     const size_t nd = grid_elems(hp);
     const size_t tb = hp.precision == WKE_FP64 ? 8 : 4, cxb = 2 * tb;
-    const size_t nf = (size_t)hp.n_groups * hp.fields_per_group;
+    const size_t nf = (size_t)hp.n_fields_total;
     void *ptr;
 #define ALLOC(field, bytes)                                  \
     do {                                                     \
@@ -441,8 +452,9 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         ALLOC(p->Vbuf[1], chunk_v_bytes(hp));
     }
     p->dp.H = p->dp.fwd_tmp = p->Hbuf[0];
-    ALLOC(p->dp.Qacc, (size_t)hp.groups_per_chunk * nd * 8);
-    ALLOC(p->dp.Qacc_im, (size_t)hp.groups_per_chunk * nd * 8);
+    ALLOC(p->dp.Qacc, (size_t)n_accumulators(hp) * nd * 8);
+    ALLOC(p->dp.Qacc_im, (size_t)n_accumulators(hp) * nd * 8);
+    ALLOC(p->dp.group_cfield, (size_t)hp.n_groups * sizeof(int));
     ALLOC(p->dp.phase, nf * hp.d * hp.N * cxb);
     ALLOC(p->dp.tw, hp.N * cxb);
     ALLOC(p->dp.tw64, hp.N_in * 16);
@@ -506,6 +518,8 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     info->d = hp.d;
     info->N = hp.N_in;
     info->N_compute = hp.N;
+    info->shared_fields = hp.shared ? 1 : 0;
+    info->units_per_collision = (int)total_units(hp);
     info->M = hp.M;
     info->precision = hp.precision;
     info->n_groups = hp.n_groups;
@@ -514,6 +528,7 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     info->groups_per_chunk = hp.groups_per_chunk;
     info->n_chunks = hp.n_chunks;
     info->launches_per_collision = 2 + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1 +
+                                   (hp.shared ? hp.n_chunks : 0) +
                                    (hp.dealias ? 1 + 2 * hp.d : 0);
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
@@ -686,7 +701,7 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
     if (t->pass2_points_per_thread != 4 && t->pass2_points_per_thread != 8 &&
         !(t->pass2_points_per_thread == 12 && plan->hp.N % 3 == 0))
         return fail(WKE_ERR_INVALID, "pass2_points_per_thread must be 4 or 8 (or 12 for N = 3 * 2^a)");
-    if (t->pass1_units_per_block < 0 || t->pass1_units_per_block > chunk_units(plan->hp, plan->hp.groups_per_chunk))
+    if (t->pass1_units_per_block < 0 || t->pass1_units_per_block > max_chunk_units(plan->hp))
         return fail(WKE_ERR_INVALID, "pass1_units_per_block must be 0..units per chunk");
     plan->hp.tune_p2_points = t->pass2_points_per_thread == 12 ? 8 : t->pass2_points_per_thread;
     plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
@@ -699,7 +714,7 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     const HostPlan &hp = plan->hp;
     std::vector<wke_tuning> cands;
     const int p2s[2] = {4, 8};
-    const int upc = chunk_units(hp, hp.groups_per_chunk);
+    const int upc = max_chunk_units(hp);
     const int p1s[4] = {0, 1, 2, 3};
     const bool p2_choice = hp.N <= 64 && hp.N % 3 != 0;
     for (int a = 0; a < (p2_choice ? 2 : 1); ++a)

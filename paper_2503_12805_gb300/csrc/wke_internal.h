@@ -54,6 +54,22 @@ struct HostPlan {
     int groups_per_chunk = 0, n_chunks = 0;
     size_t chunk_bytes = 0;
 
+    // Shared-field layout (`shared`): a chunk is a run of groups and the
+    // distinct shifted fields they need (fields with the same shift vector,
+    // e.g. the C field of one direction and an A field of another, are one
+    // field); each distinct field is transformed once per evaluation.  Units
+    // pack the chunk's fields in order (fields 2u, 2u + 1).  Pass 2
+    // transforms the units along axis 0 in place and a product pass reads
+    // every field of the chunk at each point.  In this layout field_shift
+    // lists the distinct fields of all chunks, prod_fa / prod_fb hold
+    // chunk-local field ids and group_cfield the chunk-local id of each
+    // group's C field.
+    bool shared = false;
+    std::vector<int> chunk_g0, chunk_f0;  // n_chunks + 1 entries: first group, first field
+    std::vector<int> group_cfield;        // n_groups
+    int max_chunk_fields = 0;
+    int n_fields_total = 0;               // rows of the phase table
+
     double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)
 
     // Launch layout (wke_plan_set_tuning / wke_plan_autotune).
@@ -74,6 +90,7 @@ size_t plan_device_bytes(const HostPlan &hp);
 // Arithmetic and intermediate-traffic model of one collision (for info).
 double plan_flops(const HostPlan &hp);
 double plan_l2_bytes(const HostPlan &hp);
+double total_units(const HostPlan &hp);
 
 // ---------------------------------------------------------------- kernels
 // Launch wrappers (wke_kernels_*.cu).  All are asynchronous on `stream`;
@@ -98,11 +115,24 @@ struct DevicePtrs {
     const void *Kint;         // N x N_in complex double: values on the 2N grid from the N_in grid
     const void *Kproj;        // N_in x N complex double: projection onto modes [-N_in/2, N_in/2-1]
     const int *prod_local;    // n_groups * products_per_group * 2 ints: local fields (fa, fb)
+    const int *group_cfield;  // shared-field layout: chunk-local C field of each group
     const double *prod_W;     // n_groups * products_per_group
 };
 
 // Units of a chunk of ng groups (C units first, then product units).
 inline int chunk_units(const HostPlan &hp, int ng) { return (ng + 1) / 2 + ng * hp.products_per_group; }
+// Units of chunk c in either layout; the most units any chunk has.
+inline int units_of_chunk(const HostPlan &hp, int c) {
+    if (hp.shared) return (hp.chunk_f0[c + 1] - hp.chunk_f0[c] + 1) / 2;
+    const int g0 = c * hp.groups_per_chunk;
+    return chunk_units(hp, hp.groups_per_chunk < hp.n_groups - g0 ? hp.groups_per_chunk : hp.n_groups - g0);
+}
+// FP64 accumulators of N^d points: one per group of a chunk (per-group
+// layout) or one in all (shared-field layout)
+inline int n_accumulators(const HostPlan &hp) { return hp.shared ? 1 : hp.groups_per_chunk; }
+inline int max_chunk_units(const HostPlan &hp) {
+    return hp.shared ? (hp.max_chunk_fields + 1) / 2 : chunk_units(hp, hp.groups_per_chunk);
+}
 size_t chunk_unit_bytes(const HostPlan &hp);   // H buffer bytes for a full chunk
 size_t chunk_v_bytes(const HostPlan &hp);      // V buffer bytes for a full chunk
 

@@ -170,9 +170,16 @@ __global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict
 
 // ------------------------------------------------------------------ pass 1
 // Global field indices (fa, fb) of unit u of the chunk starting at group g0
-// with ng groups; fb = -1 for a lone C unit.
+// with ng groups; fb = -1 for a lone field.  In the shared-field layout
+// (sf0 >= 0) the chunk's fields are sf0 .. sf0 + sK - 1 and unit u packs
+// fields 2u and 2u + 1.
 __device__ __forceinline__ void unit_fields(int u, int g0, int ng, int FPG, int PPG, const int *__restrict__ prod_local,
-                                            int &fa, int &fb) {
+                                            int sf0, int sK, int &fa, int &fb) {
+    if (sf0 >= 0) {
+        fa = sf0 + 2 * u;
+        fb = 2 * u + 1 < sK ? fa + 1 : -1;
+        return;
+    }
     const int ncu = (ng + 1) >> 1;
     if (u < ncu) {
         const int ga = g0 + 2 * u;
@@ -207,7 +214,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
 k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
            const cx<T> *__restrict__ tw_g, const int *__restrict__ prod_local, int g0, int ng, int FPG, int PPG,
-           int nunits, int units_per_block) {
+           int nunits, int units_per_block, int sf0, int sK) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -228,7 +235,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     // rows 1 and 2 of unit u's phase tables: prow[buf][0, 2N) field a, [2N, 4N) field b
     auto stage_rows = [&](int u) {
         int fa, fb;
-        unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+        unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
         const cx<T> *pa = phase + (size_t)fa * 3 * N + N;
         const cx<T> *pb = phase + (size_t)(fb >= 0 ? fb : fa) * 3 * N + N;
         cx<T> *dst = prow + ((u - ubeg) & 1) * 4 * N;
@@ -243,7 +250,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     for (int e = 0; e < E; ++e) g[e] = grow[t + e * TPL];
     for (int u = ubeg; u < uend; ++u) {
         int fa, fb;
-        unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+        unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
         if (u + 1 < uend) stage_rows(u + 1);   // into the buffer unit u - 1 used
         else cp_async_commit();
         cp_async_wait<1>();
@@ -281,7 +288,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
 template <typename T, int N>
 __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ H,
                            const cx<T> *__restrict__ tw_g, const int *__restrict__ prod_local, int g0, int ng,
-                           int FPG, int PPG) {
+                           int FPG, int PPG, int sf0, int sK) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,7 +302,7 @@ __global__ void k_pass1_2d(const cx<T> *__restrict__ ghat, const cx<T> *__restri
     const int u = blockIdx.y;
     cx<T> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     int fa, fb;
-    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
     const cx<T> *pa = phase + (size_t)fa * 2 * N;
     const cx<T> a0 = pa[j1];
     cx<T> v[E];
@@ -344,7 +351,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
 k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T> *__restrict__ tw_g,
              const cx<T> *__restrict__ nslice, const int *__restrict__ prod_local, int G, int n_groups, int FPG,
-             int PPG, int units_per_chunk, int chunk0) {
+             int PPG, int units_per_chunk, int chunk0, int sf0, int sK) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH, H2 = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -360,13 +367,13 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     const size_t NN = (size_t)N * N;
     const int ax = blockIdx.x, u = blockIdx.y;
     const int g0 = (chunk0 + blockIdx.z) * G, ng = min(G, n_groups - g0);
-    if (u >= (ng + 1) / 2 + ng * PPG) return;   // block-uniform
+    if (u >= (sf0 >= 0 ? (sK + 1) / 2 : (ng + 1) / 2 + ng * PPG)) return;   // block-uniform
     V += (size_t)blockIdx.z * units_per_chunk * 3 * NN;
     const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
     const int mrow = (N - row) % N;
     const cx<T> *S = nslice + (size_t)ax * NN;
     int fa, fb;
-    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
     const cx<T> *pa = phase + (size_t)fa * 3 * N;
     const cx<T> ca = pa[ax * N + H2];
     const cx<T> ra = cmul<T>(ca, pa[b0 * N + row]), rma = cmul<T>(ca, pa[b0 * N + mrow]);
@@ -403,7 +410,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(32)
 k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T> *__restrict__ tw_g,
              const cx<T> *__restrict__ nslice, const int *__restrict__ prod_local, int G, int n_groups, int FPG,
-             int PPG, int units_per_chunk, int chunk0) {
+             int PPG, int units_per_chunk, int chunk0, int sf0, int sK) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, H2 = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -413,7 +420,7 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     const int lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int g0 = (chunk0 + blockIdx.y) * G, ng = min(G, n_groups - g0);
-    const int nitems = 2 * ((ng + 1) / 2 + ng * PPG);
+    const int nitems = 2 * (sf0 >= 0 ? (sK + 1) / 2 : (ng + 1) / 2 + ng * PPG);
     V += (size_t)blockIdx.y * units_per_chunk * 2 * N;
     const int item = blockIdx.x * LPW + c;
     const bool valid = item < nitems;
@@ -421,7 +428,7 @@ k_nyquist_2d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     const int u = it >> 1, ax = it & 1;
     const int b = 1 - ax;
     int fa, fb;
-    unit_fields(u, g0, ng, FPG, PPG, prod_local, fa, fb);
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
     const cx<T> *pa = phase + (size_t)fa * 2 * N;
     const cx<T> *pb = fb >= 0 ? phase + (size_t)fb * 2 * N : pa;
     const cx<T> ca = pa[ax * N + H2], cb = pb[ax * N + H2];
@@ -632,6 +639,106 @@ k_pass2(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__
         double *Qig = Qim + (size_t)gl * ND;
 #pragma unroll
         for (int e = 0; e < E; ++e) Qig[(size_t)(t + e * TPL) * P + col] += (double)ai[e];
+    }
+}
+
+// ------------------------------------------------------------------ shared-field layout
+// Pass 2: axis-0 inverse transform of every unit of the chunk, in place.
+// Block (column tile, unit); the tile layout of pass 2.
+template <typename T, int N, int EP>
+__global__ void __launch_bounds__(Pass2Cfg<T, N, EP>::THREADS)
+k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
+    typedef Pass2Cfg<T, N, EP> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
+    load_twiddles<T, N>(tw, tw_g);
+    const int z = threadIdx.x % CB, t = threadIdx.x / CB;
+    const int col = blockIdx.x * CB + z;
+    cx<T> *Hu = H + (size_t)blockIdx.y * N * P + col;
+    cx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = Hu[(size_t)(t + e * TPL) * P];
+    col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) Hu[(size_t)(t + e * TPL) * P] = v[e];
+}
+
+// Product pass: one grid point per thread and loop.  The chunk's K fields at
+// the point are unpacked from the transformed units (real-slot field
+// (Re Z + b) + i a, imaginary-slot field (Im Z - a) + i b, a and b the
+// Nyquist imaginary parts) into this thread's column of shared memory; then
+// every group g of the chunk adds, with s = C + F and cf = C F,
+//   sum_p W_p Re[(A_p B_p) s - cf (A_p + B_p)]   (and Im on request).
+// The group sums are added in T with compensation (Neumaier) and the chunk's
+// total goes to the single FP64 accumulator: one addition per point per
+// chunk, in chunk order, so the result is deterministic.
+constexpr int kProductThreads = 128;
+
+template <typename T, bool IM, bool NYQ>
+__global__ void __launch_bounds__(kProductThreads)
+k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
+           double *__restrict__ Qacc, double *__restrict__ Qim, const int *__restrict__ group_cfield,
+           const int *__restrict__ prod_local, const double *__restrict__ prod_W, int d, int N, int P,
+           int g0, int ng, int K, int PPG) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *fb = reinterpret_cast<cx<T> *>(smem_raw) + threadIdx.x;   // field k at fb[k * blockDim.x]
+    const int stride = blockDim.x;
+    const size_t ND = (size_t)N * P;
+    const size_t VS = (size_t)d * P;          // Nyquist table entries per unit
+    const int U = (K + 1) / 2;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < ND; idx += (size_t)gridDim.x * blockDim.x) {
+        const int i1 = (int)(idx / P), col = (int)(idx - (size_t)i1 * P);
+        const T sgn1 = (i1 & 1) ? (T)-1 : (T)1;
+        for (int u = 0; u < U; ++u) {
+            const cx<T> Z = H[(size_t)u * ND + idx];
+            T a = (T)0, b = (T)0;
+            if (NYQ) {
+                const cx<T> *Vu = Vtab + (size_t)u * VS;
+                if (d == 3) {
+                    const int i2 = col / N, i3 = col - i2 * N;
+                    const T sg2 = (i2 & 1) ? (T)-1 : (T)1, sg3 = (i3 & 1) ? (T)-1 : (T)1;
+                    const cx<T> v0 = Vu[col], v1 = Vu[N * N + i1 * N + i3], v2 = Vu[2 * N * N + i1 * N + i2];
+                    a = sgn1 * v0.x + sg2 * v1.x + sg3 * v2.x;
+                    b = sgn1 * v0.y + sg2 * v1.y + sg3 * v2.y;
+                } else {
+                    const T sg2 = (col & 1) ? (T)-1 : (T)1;
+                    const cx<T> v0 = Vu[col], v1 = Vu[N + i1];
+                    a = sgn1 * v0.x + sg2 * v1.x;
+                    b = sgn1 * v0.y + sg2 * v1.y;
+                }
+            }
+            fb[(2 * u) * stride] = mkc<T>(Z.x + b, a);
+            if (2 * u + 1 < K) fb[(2 * u + 1) * stride] = mkc<T>(Z.y - a, b);
+        }
+        const T F = f[idx];
+        T sum = (T)0, comp = (T)0, sumi = (T)0, compi = (T)0;
+        for (int g = g0; g < g0 + ng; ++g) {
+            const cx<T> C = fb[group_cfield[g] * stride];
+            const T sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
+            T acc = (T)0, acci = (T)0;
+            for (int p = 0; p < PPG; ++p) {
+                const int slot = g * PPG + p;
+                const T W = (T)prod_W[slot];
+                const cx<T> A = fb[prod_local[2 * slot] * stride], B = fb[prod_local[2 * slot + 1] * stride];
+                const T pr = A.x * B.x - A.y * B.y, pim = A.x * B.y + A.y * B.x;   // A B
+                const T ur = A.x + B.x, ui = A.y + B.y;                            // A + B
+                acc += W * ((pr * sr - pim * si) - (cr * ur - ci * ui));
+                if (IM) acci += W * ((pr * si + pim * sr) - (cr * ui + ci * ur));
+            }
+            // Neumaier summation of the group sums
+            T tsum = sum + acc;
+            comp += fabs(sum) >= fabs(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+            sum = tsum;
+            if (IM) {
+                tsum = sumi + acci;
+                compi += fabs(sumi) >= fabs(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+                sumi = tsum;
+            }
+        }
+        Qacc[idx] += (double)sum + (double)comp;
+        if (IM) Qim[idx] += (double)sumi + (double)compi;
     }
 }
 

@@ -68,10 +68,33 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
 }
 
 // ------------------------------------------------------------------ pass 1
+// Groups, fields and units of chunk c: per-group layout (g0, ng; sf0 = -1)
+// or shared-field layout (fields sf0 .. sf0 + sK - 1).
+struct ChunkRange {
+    int g0, ng, sf0, sK, units;
+};
+static inline ChunkRange chunk_range(const HostPlan &hp, int c) {
+    ChunkRange r;
+    if (hp.shared) {
+        r.g0 = hp.chunk_g0[c];
+        r.ng = hp.chunk_g0[c + 1] - r.g0;
+        r.sf0 = hp.chunk_f0[c];
+        r.sK = hp.chunk_f0[c + 1] - r.sf0;
+    } else {
+        r.g0 = c * hp.groups_per_chunk;
+        r.ng = std::min(hp.groups_per_chunk, hp.n_groups - r.g0);
+        r.sf0 = -1;
+        r.sK = 0;
+    }
+    r.units = units_of_chunk(hp, c);
+    return r;
+}
+
 template <typename T, int N>
-static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
     typedef LineCfg<T, N> Cfg;
-    const int nunits = chunk_units(hp, ng);
+    const ChunkRange cr = chunk_range(hp, c);
+    const int g0 = cr.g0, ng = cr.ng, nunits = cr.units;
     const cx<T> *ghat = static_cast<const cx<T> *>(p.ghat);
     const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
     cx<T> *H = static_cast<cx<T> *>(p.H);
@@ -85,7 +108,8 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
             const int upb = std::min(nunits, hp.tune_p1_units_per_block > 0 ? hp.tune_p1_units_per_block : 3);
             dim3 grid(N, (nunits + upb - 1) / upb);
             k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng,
-                                                               hp.fields_per_group, hp.products_per_group, nunits, upb);
+                                                               hp.fields_per_group, hp.products_per_group, nunits, upb,
+                                                               cr.sf0, cr.sK);
         } else {
             return (int)cudaErrorInvalidValue;
         }
@@ -95,17 +119,18 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cuda
         if ((rc = set_smem(k_pass1_2d<T, N>, smem))) return rc;
         dim3 grid(N / (warps * Cfg::LPW), nunits);
         k_pass1_2d<T, N><<<grid, warps * 32, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng, hp.fields_per_group,
-                                                        hp.products_per_group);
+                                                        hp.products_per_group, cr.sf0, cr.sK);
     }
     return (int)cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ Nyquist tables
-// Tables of every unit of chunks [chunk0, chunk0 + nchunks), into p.V.
+// Tables of every unit of chunk c, into p.V.
 template <typename T, int N>
-static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nchunks, cudaStream_t s) {
+static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
     typedef LineCfg<T, N> Cfg;
-    const int upc = chunk_units(hp, hp.groups_per_chunk);
+    const ChunkRange cr = chunk_range(hp, c);
+    const int upc = max_chunk_units(hp), chunk0 = hp.shared ? 0 : c, nchunks = 1;
     const cx<T> *ph = static_cast<const cx<T> *>(p.phase);
     cx<T> *V = static_cast<cx<T> *>(p.V);
     const cx<T> *tw = static_cast<const cx<T> *>(p.tw);
@@ -117,7 +142,7 @@ static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nc
             if ((rc = set_smem(k_nyquist_3d<T, N>, smem))) return rc;
             k_nyquist_3d<T, N><<<dim3(3, upc, nchunks), N * Cfg::TPL, smem, s>>>(
                 ph, V, tw, ns, p.prod_local, hp.groups_per_chunk, hp.n_groups, hp.fields_per_group,
-                hp.products_per_group, upc, chunk0);
+                hp.products_per_group, upc, chunk0, cr.sf0, cr.sK);
         } else {
             return (int)cudaErrorInvalidValue;
         }
@@ -126,14 +151,64 @@ static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nc
         if ((rc = set_smem(k_nyquist_2d<T, N>, smem))) return rc;
         k_nyquist_2d<T, N><<<dim3((2 * upc + Cfg::LPW - 1) / Cfg::LPW, nchunks), 32, smem, s>>>(
             ph, V, tw, ns, p.prod_local, hp.groups_per_chunk, hp.n_groups, hp.fields_per_group,
-            hp.products_per_group, upc, chunk0);
+            hp.products_per_group, upc, chunk0, cr.sf0, cr.sK);
     }
     return (int)cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ shared-field layout
+template <typename T, int N, int EP> static int axis0_ne(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    typedef Pass2Cfg<T, N, EP> Cfg;
+    const int P = cols_of(hp);
+    int CB = std::min(Cfg::CB, P);
+    while (P % CB) CB /= 2;
+    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB) * sizeof(cx<T>);
+    int rc = 0;
+    if ((rc = set_smem(k_axis0<T, N, EP>, smem))) return rc;
+    k_axis0<T, N, EP><<<dim3(P / CB, units_of_chunk(hp, c)), CB * Cfg::TPL, smem, s>>>(
+        static_cast<cx<T> *>(p.H), static_cast<const cx<T> *>(p.tw), P, CB);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int N> static int axis0_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    if constexpr (N % 3 == 0) {
+        return axis0_ne<T, N, 12>(hp, p, c, s);
+    } else {
+        if constexpr (N <= 64) {
+            if (hp.tune_p2_points == 8) return axis0_ne<T, N, 8>(hp, p, c, s);
+        }
+        return axis0_ne<T, N, 4>(hp, p, c, s);
+    }
+}
+
+template <typename T, bool IM, bool NYQ>
+static int products_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    const ChunkRange cr = chunk_range(hp, c);
+    const int P = cols_of(hp);
+    const size_t ND = nd_of(hp);
+    const size_t smem = (size_t)cr.sK * kProductThreads * sizeof(cx<T>);
+    int rc = 0;
+    if ((rc = set_smem(k_products<T, IM, NYQ>, smem))) return rc;
+    const int blocks = (int)std::min<size_t>((ND + kProductThreads - 1) / kProductThreads, 152 * 16);
+    k_products<T, IM, NYQ><<<blocks, kProductThreads, smem, s>>>(
+        static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
+        p.Qacc_im, p.group_cfield, p.prod_local, p.prod_W, hp.d, hp.N, P, cr.g0, cr.ng, cr.sK,
+        hp.products_per_group);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int products_T(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
+    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
+    if (nyq) return im ? products_nim<T, true, true>(hp, p, c, s) : products_nim<T, false, true>(hp, p, c, s);
+    return im ? products_nim<T, true, false>(hp, p, c, s) : products_nim<T, false, false>(hp, p, c, s);
+}
+
 // ------------------------------------------------------------------ pass 2
 template <typename T, int N, int EP, bool IM, bool NYQ>
-static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    const ChunkRange cr = chunk_range(hp, c);
+    const int g0 = cr.g0, ng = cr.ng;
     typedef Pass2Cfg<T, N, EP> Cfg;
     const int P = cols_of(hp);
     int CB = std::min(Cfg::CB, P);             // columns per block: a power of two dividing P
@@ -153,22 +228,22 @@ static int pass2_nim(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cu
 }
 
 template <typename T, int N, int EP>
-static int pass2_ne(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+static int pass2_ne(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
     const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
     if (nyq)
-        return im ? pass2_nim<T, N, EP, true, true>(hp, p, g0, ng, s) : pass2_nim<T, N, EP, false, true>(hp, p, g0, ng, s);
-    return im ? pass2_nim<T, N, EP, true, false>(hp, p, g0, ng, s) : pass2_nim<T, N, EP, false, false>(hp, p, g0, ng, s);
+        return im ? pass2_nim<T, N, EP, true, true>(hp, p, c, s) : pass2_nim<T, N, EP, false, true>(hp, p, c, s);
+    return im ? pass2_nim<T, N, EP, true, false>(hp, p, c, s) : pass2_nim<T, N, EP, false, false>(hp, p, c, s);
 }
 
 template <typename T, int N>
-static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+static int pass2_n(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
     if constexpr (N % 3 == 0) {
-        return pass2_ne<T, N, 12>(hp, p, g0, ng, im, s);
+        return pass2_ne<T, N, 12>(hp, p, c, im, s);
     } else {
         if constexpr (N <= 64) {
-            if (hp.tune_p2_points == 8) return pass2_ne<T, N, 8>(hp, p, g0, ng, im, s);
+            if (hp.tune_p2_points == 8) return pass2_ne<T, N, 8>(hp, p, c, im, s);
         }
-        return pass2_ne<T, N, 4>(hp, p, g0, ng, im, s);
+        return pass2_ne<T, N, 4>(hp, p, c, im, s);
     }
 }
 
@@ -186,42 +261,55 @@ template <typename T> int forward_T(const HostPlan &hp, const DevicePtrs &p, cud
     return (int)cudaErrorInvalidValue;
 }
 
-template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, cudaStream_t s) {
+template <typename T> int pass1_T(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
     switch (hp.N) {
-        case 16: return pass1_n<T, 16>(hp, p, g0, ng, s);
-        case 32: return pass1_n<T, 32>(hp, p, g0, ng, s);
-        case 48: return pass1_n<T, 48>(hp, p, g0, ng, s);
-        case 64: return pass1_n<T, 64>(hp, p, g0, ng, s);
-        case 96: return pass1_n<T, 96>(hp, p, g0, ng, s);
-        case 128: return pass1_n<T, 128>(hp, p, g0, ng, s);
-        case 256: return pass1_n<T, 256>(hp, p, g0, ng, s);
+        case 16: return pass1_n<T, 16>(hp, p, c, s);
+        case 32: return pass1_n<T, 32>(hp, p, c, s);
+        case 48: return pass1_n<T, 48>(hp, p, c, s);
+        case 64: return pass1_n<T, 64>(hp, p, c, s);
+        case 96: return pass1_n<T, 96>(hp, p, c, s);
+        case 128: return pass1_n<T, 128>(hp, p, c, s);
+        case 256: return pass1_n<T, 256>(hp, p, c, s);
     }
     return (int)cudaErrorInvalidValue;
 }
 
-template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int chunk0, int nchunks, cudaStream_t s) {
+template <typename T> int nyquist_T(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
     switch (hp.N) {
-        case 16: return nyquist_n<T, 16>(hp, p, chunk0, nchunks, s);
-        case 32: return nyquist_n<T, 32>(hp, p, chunk0, nchunks, s);
-        case 48: return nyquist_n<T, 48>(hp, p, chunk0, nchunks, s);
-        case 64: return nyquist_n<T, 64>(hp, p, chunk0, nchunks, s);
-        case 96: return nyquist_n<T, 96>(hp, p, chunk0, nchunks, s);
-        case 128: return nyquist_n<T, 128>(hp, p, chunk0, nchunks, s);
-        case 256: return nyquist_n<T, 256>(hp, p, chunk0, nchunks, s);
+        case 16: return nyquist_n<T, 16>(hp, p, c, s);
+        case 32: return nyquist_n<T, 32>(hp, p, c, s);
+        case 48: return nyquist_n<T, 48>(hp, p, c, s);
+        case 64: return nyquist_n<T, 64>(hp, p, c, s);
+        case 96: return nyquist_n<T, 96>(hp, p, c, s);
+        case 128: return nyquist_n<T, 128>(hp, p, c, s);
+        case 256: return nyquist_n<T, 256>(hp, p, c, s);
     }
     return (int)cudaErrorInvalidValue;
 }
 
 template <typename T>
-int pass2_T(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, bool im, cudaStream_t s) {
+int pass2_T(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
     switch (hp.N) {
-        case 16: return pass2_n<T, 16>(hp, p, g0, ng, im, s);
-        case 32: return pass2_n<T, 32>(hp, p, g0, ng, im, s);
-        case 48: return pass2_n<T, 48>(hp, p, g0, ng, im, s);
-        case 64: return pass2_n<T, 64>(hp, p, g0, ng, im, s);
-        case 96: return pass2_n<T, 96>(hp, p, g0, ng, im, s);
-        case 128: return pass2_n<T, 128>(hp, p, g0, ng, im, s);
-        case 256: return pass2_n<T, 256>(hp, p, g0, ng, im, s);
+        case 16: return pass2_n<T, 16>(hp, p, c, im, s);
+        case 32: return pass2_n<T, 32>(hp, p, c, im, s);
+        case 48: return pass2_n<T, 48>(hp, p, c, im, s);
+        case 64: return pass2_n<T, 64>(hp, p, c, im, s);
+        case 96: return pass2_n<T, 96>(hp, p, c, im, s);
+        case 128: return pass2_n<T, 128>(hp, p, c, im, s);
+        case 256: return pass2_n<T, 256>(hp, p, c, im, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T> int axis0_T(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return axis0_n<T, 16>(hp, p, c, s);
+        case 32: return axis0_n<T, 32>(hp, p, c, s);
+        case 48: return axis0_n<T, 48>(hp, p, c, s);
+        case 64: return axis0_n<T, 64>(hp, p, c, s);
+        case 96: return axis0_n<T, 96>(hp, p, c, s);
+        case 128: return axis0_n<T, 128>(hp, p, c, s);
+        case 256: return axis0_n<T, 256>(hp, p, c, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -231,7 +319,7 @@ int finalize_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cuda
     const size_t ND = nd_of(hp);
     const int threads = 256;
     const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
-    k_finalize<T><<<blocks, threads, 0, s>>>(p.Qacc, Qim ? p.Qacc_im : nullptr, hp.groups_per_chunk, ND, hp.scale,
+    k_finalize<T><<<blocks, threads, 0, s>>>(p.Qacc, Qim ? p.Qacc_im : nullptr, n_accumulators(hp), ND, hp.scale,
                                              static_cast<T *>(Q), static_cast<T *>(Qim));
     return (int)cudaGetLastError();
 }
@@ -306,7 +394,7 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     const int threads = 256;
     const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
     double *qf = static_cast<double *>(p.map0);
-    k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, hp.groups_per_chunk, ND, hp.scale, qf, nullptr);
+    k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, n_accumulators(hp), ND, hp.scale, qf, nullptr);
     int rc = (int)cudaGetLastError();
     const int n = hp.N, m = hp.N_in;
     const double2 *K = static_cast<const double2 *>(p.Kproj);
@@ -327,9 +415,11 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     template int dealias_prepare_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                 \
     template int dealias_finish_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);  \
     template int forward_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                         \
-    template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);                 \
-    template int nyquist_T<T>(const HostPlan &, const DevicePtrs &, int, int, cudaStream_t);               \
-    template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, int, bool, cudaStream_t);           \
+    template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                      \
+    template int nyquist_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                    \
+    template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);                \
+    template int axis0_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                      \
+    template int products_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);             \
     template int finalize_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);        \
     template int moments_T<T>(const HostPlan &, const void *, double *, double *, cudaStream_t);           \
     template int rk_stage_T<T>(const HostPlan &, const void *, const void *, double *, void *, double,     \

@@ -170,6 +170,152 @@ static bool compiled_length(int d, int N) {
     return N == 16 || N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 256;
 }
 
+// Shared-field layout: chunks of consecutive groups whose distinct fields
+// stay within the product pass's limit (96 in FP32, 48 in FP64: the fields of
+// a point are held in shared memory, 96 KB per block of 128 threads) and
+// whose units fit the byte budget.
+// Fields are the same when their shift vectors agree to 1e-12 (relative);
+// the first one's shift is used.  With `force` false the layout is kept only
+// when it transforms at least 15% fewer units than the per-group layout.
+static int build_shared_layout(HostPlan &hp, bool force) {
+    const int d = hp.d, FPG = hp.fields_per_group, PPG = hp.products_per_group;
+    const int kMaxChunkFields = hp.precision == WKE_FP64 ? 48 : 96;
+    size_t nd = 1;
+    for (int a = 0; a < d; ++a) nd *= (size_t)hp.N;
+    const size_t unit_bytes = nd * (hp.precision == WKE_FP64 ? 16 : 8);
+    const size_t max_units = std::max<size_t>(1, hp.chunk_bytes / unit_bytes);
+
+    std::vector<double> shifts;              // distinct fields of all chunks, d each
+    std::vector<int> chunk_g0{0}, chunk_f0{0}, cfield(hp.n_groups);
+    std::vector<int> pfa(hp.prod_fa.size()), pfb(hp.prod_fb.size());
+    auto find = [&](const double *x, int f0, int f1) {
+        for (int f = f0; f < f1; ++f) {
+            bool same = true;
+            for (int a = 0; a < d && same; ++a) {
+                const double y = shifts[(size_t)f * d + a];
+                same = std::fabs(y - x[a]) <= 1e-12 * (1.0 + std::fabs(x[a]));
+            }
+            if (same) return f;
+        }
+        return -1;
+    };
+    // local fields of group g that its C and its products use
+    auto used_fields = [&](int g) {
+        std::vector<int> loc{0};
+        for (int p = 0; p < PPG; ++p) {
+            const size_t slot = (size_t)g * PPG + p;
+            if (hp.prod_W[slot] == 0.0) continue;        // padding product
+            loc.push_back(hp.prod_fa[slot]);
+            loc.push_back(hp.prod_fb[slot]);
+        }
+        return loc;
+    };
+    // distinct fields of groups [ga, gb)
+    auto count_distinct = [&](int ga, int gb) {
+        std::vector<const double *> seen;
+        for (int g = ga; g < gb; ++g) {
+            const double *fs = &hp.field_shift[(size_t)g * FPG * d];
+            for (int l : used_fields(g)) {
+                const double *x = fs + (size_t)l * d;
+                bool dup = false;
+                for (const double *y : seen) {
+                    bool same = true;
+                    for (int a = 0; a < d && same; ++a) same = std::fabs(y[a] - x[a]) <= 1e-12 * (1.0 + std::fabs(x[a]));
+                    if (same) {
+                        dup = true;
+                        break;
+                    }
+                }
+                if (!dup) seen.push_back(x);
+            }
+        }
+        return (int)seen.size();
+    };
+    auto fits = [&](int K) { return K <= kMaxChunkFields && (size_t)((K + 1) / 2) <= max_units; };
+    // Chunk boundaries: whole radial shells (the n_s groups of one radius,
+    // which share most fields) while they fit; a shell too large alone is
+    // split group by group.
+    std::vector<int> bounds{0};
+    while (bounds.back() < hp.n_groups) {
+        const int start = bounds.back();
+        int end = start;
+        while (end < hp.n_groups) {
+            const int shell_end = std::min(hp.n_groups, (end / hp.n_s + 1) * hp.n_s);
+            if (!fits(count_distinct(start, shell_end))) break;
+            end = shell_end;
+        }
+        if (end == start) {
+            while (end < hp.n_groups && fits(count_distinct(start, end + 1))) ++end;
+            if (end == start) end = start + 1;      // one group always forms a chunk
+        }
+        bounds.push_back(end);
+    }
+    int max_fields = 0;
+    size_t next_bound = 1;
+    for (int g = 0; g < hp.n_groups; ++g) {
+        if (g == bounds[next_bound - 1] && g > 0) {
+            chunk_g0.push_back(g);
+            chunk_f0.push_back((int)(shifts.size() / d));
+        }
+        if (g + 1 == bounds[next_bound]) ++next_bound;
+        const double *fs = &hp.field_shift[(size_t)g * FPG * d];
+        const int c0 = chunk_f0.back();
+        auto field_of = [&](int l) {
+            const double *x = fs + (size_t)l * d;
+            int f = find(x, c0, (int)(shifts.size() / d));
+            if (f < 0) {
+                f = (int)(shifts.size() / d);
+                shifts.insert(shifts.end(), x, x + d);
+            }
+            return f - c0;
+        };
+        cfield[g] = field_of(0);
+        for (int p = 0; p < PPG; ++p) {
+            const size_t slot = (size_t)g * PPG + p;
+            if (hp.prod_W[slot] == 0.0) {
+                pfa[slot] = pfb[slot] = cfield[g];       // zero weight: any field of the chunk
+                continue;
+            }
+            pfa[slot] = field_of(hp.prod_fa[slot]);
+            pfb[slot] = field_of(hp.prod_fb[slot]);
+        }
+        max_fields = std::max(max_fields, (int)(shifts.size() / d) - c0);
+    }
+    chunk_g0.push_back(hp.n_groups);
+    chunk_f0.push_back((int)(shifts.size() / d));
+    const int n_chunks = (int)chunk_g0.size() - 1;
+
+    double shared_units = 0, group_units = 0;
+    for (int c = 0; c < n_chunks; ++c) shared_units += (chunk_f0[c + 1] - chunk_f0[c] + 1) / 2;
+    for (int c = 0; c < hp.n_chunks; ++c) {
+        const int g0 = c * hp.groups_per_chunk;
+        group_units += chunk_units(hp, std::min(hp.groups_per_chunk, hp.n_groups - g0));
+    }
+    if (max_fields > kMaxChunkFields) {
+        if (force)
+            return fail(WKE_ERR_UNSUPPORTED, "shared-field layout: one group needs " + std::to_string(max_fields) +
+                                                 " fields, more than the product pass holds (" +
+                                                 std::to_string(kMaxChunkFields) + ")");
+        return WKE_OK;
+    }
+    if (!force && shared_units > 0.85 * group_units) return WKE_OK;
+
+    hp.shared = true;
+    hp.field_shift = shifts;
+    hp.n_fields_total = (int)(shifts.size() / d);
+    hp.prod_fa = pfa;
+    hp.prod_fb = pfb;
+    hp.group_cfield = cfield;
+    hp.chunk_g0 = chunk_g0;
+    hp.chunk_f0 = chunk_f0;
+    hp.n_chunks = n_chunks;
+    hp.max_chunk_fields = max_fields;
+    int gmax = 0;
+    for (int c = 0; c < n_chunks; ++c) gmax = std::max(gmax, chunk_g0[c + 1] - chunk_g0[c]);
+    hp.groups_per_chunk = gmax;
+    return WKE_OK;
+}
+
 int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, HostPlan &hp) {
     if (!quad) return fail(WKE_ERR_INVALID, "quadrature descriptor is NULL");
     if (d != 2 && d != 3) return fail(WKE_ERR_INVALID, "d must be 2 or 3");
@@ -371,6 +517,14 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     hp.groups_per_chunk = (int)std::max<size_t>(1, 2 * (hp.chunk_bytes / per_pair));
     hp.groups_per_chunk = std::min(hp.groups_per_chunk, hp.n_groups);
     hp.n_chunks = (hp.n_groups + hp.groups_per_chunk - 1) / hp.groups_per_chunk;
+    hp.n_fields_total = hp.n_groups * hp.fields_per_group;
+
+    if (quad->layout != WKE_LAYOUT_AUTO && quad->layout != WKE_LAYOUT_PER_GROUP && quad->layout != WKE_LAYOUT_SHARED)
+        return fail(WKE_ERR_INVALID, "layout must be WKE_LAYOUT_AUTO, _PER_GROUP or _SHARED");
+    if (quad->layout != WKE_LAYOUT_PER_GROUP) {
+        int rc2 = build_shared_layout(hp, quad->layout == WKE_LAYOUT_SHARED);
+        if (rc2) return rc2;
+    }
 
     hp.scale = std::ldexp(1.0, 1 - d) * (hp.dispersion == WKE_OMEGA_K2 ? 0.5 : 1.0);
     return WKE_OK;
@@ -389,12 +543,12 @@ static size_t grid_size(const HostPlan &hp);
 
 size_t chunk_unit_bytes(const HostPlan &hp) {
     size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
-    return std::max((size_t)chunk_units(hp, hp.groups_per_chunk) * grid_size(hp) * cxb, grid_size(hp) * 16);
+    return std::max((size_t)max_chunk_units(hp) * grid_size(hp) * cxb, grid_size(hp) * 16);
 }
 
 size_t chunk_v_bytes(const HostPlan &hp) {
     size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;   // a unit's two fields interleaved
-    return (size_t)chunk_units(hp, hp.groups_per_chunk) * hp.d * (grid_size(hp) / hp.N) * cxb;
+    return (size_t)max_chunk_units(hp) * hp.d * (grid_size(hp) / hp.N) * cxb;
 }
 
 static size_t grid_size(const HostPlan &hp) {
@@ -407,12 +561,13 @@ size_t plan_device_bytes(const HostPlan &hp) {
     size_t nd = grid_size(hp);
     size_t tb = hp.precision == WKE_FP64 ? 8 : 4;
     size_t cxb = 2 * tb;
-    size_t n_fields = (size_t)hp.n_groups * hp.fields_per_group;
+    size_t n_fields = (size_t)hp.n_fields_total;
     size_t bytes = 0;
     bytes += nd * cxb + hp.d * (nd / hp.N) * cxb;                       // ghat, Nyquist slices
     bytes += 2 * chunk_unit_bytes(hp);                                   // H double-buffered
     if (hp.nyquist == WKE_NYQ_KEEP) bytes += 2 * chunk_v_bytes(hp);      // Nyquist tables, double-buffered
-    bytes += 2 * (size_t)hp.groups_per_chunk * nd * 8;                 // Qacc, Qacc_im
+    bytes += 2 * (size_t)(hp.shared ? 1 : hp.groups_per_chunk) * nd * 8;   // Qacc, Qacc_im
+    bytes += (size_t)hp.n_groups * sizeof(int);                         // C field of each group
     bytes += n_fields * hp.d * hp.N * cxb;                              // phase tables
     bytes += hp.N * cxb + hp.N * 16;                                    // twiddles
     bytes += (size_t)hp.n_groups * hp.products_per_group * 2 * sizeof(int);
@@ -428,13 +583,10 @@ size_t plan_device_bytes(const HostPlan &hp) {
     return bytes;
 }
 
-// Units transformed per evaluation (C units of every chunk + product units).
-static double total_units(const HostPlan &hp) {
+// Units transformed per evaluation.
+double total_units(const HostPlan &hp) {
     double u = 0;
-    for (int c = 0; c < hp.n_chunks; ++c) {
-        int ng = std::min(hp.groups_per_chunk, hp.n_groups - c * hp.groups_per_chunk);
-        u += chunk_units(hp, ng);
-    }
+    for (int c = 0; c < hp.n_chunks; ++c) u += units_of_chunk(hp, c);
     return u;
 }
 
@@ -442,7 +594,7 @@ double plan_flops(const HostPlan &hp) {
     double nd = (double)grid_size(hp);
     double lg = std::log2(nd);
     double units = total_units(hp);
-    double n_fields = (double)hp.n_groups * hp.fields_per_group;
+    double n_fields = 2.0 * units;
     double n_prod = (double)hp.n_groups * hp.products_per_group;
     double nin = std::pow((double)hp.N_in, hp.d);
     double fwd = 5.0 * nin * std::log2(nin);
@@ -454,9 +606,12 @@ double plan_flops(const HostPlan &hp) {
         fwd += maps;
     }
     double inv = units * 5.0 * nd * lg;                    // pass 1 + pass 2 transforms
-    double c_units = units - (double)hp.n_groups * hp.products_per_group;
-    double c_again = ((double)hp.n_groups - c_units) * 5.0 * nd * std::log2((double)hp.N);  // shared C units, axis 0
-    double nyq = hp.nyquist == WKE_NYQ_KEEP ? n_fields * hp.d * 5.0 * (nd / hp.N) * std::log2(nd / hp.N) : 0.0;
+    // per-group layout: pass 2 transforms each group's C unit once per group
+    double c_again = hp.shared ? 0.0
+                               : ((double)hp.n_groups - (units - n_prod)) * 5.0 * nd * std::log2((double)hp.N);
+    (void)n_fields;
+    // Nyquist tables: d transforms of N^{d-1} points per unit (two fields each)
+    double nyq = hp.nyquist == WKE_NYQ_KEEP ? units * hp.d * 5.0 * (nd / hp.N) * std::log2(nd / hp.N) : 0.0;
     double phases = units * nd * 16.0;                     // two phase products and the packing per point
     double prods = n_prod * nd * 30.0;                     // cubic product, weight, accumulate
     return fwd + inv + c_again + nyq + phases + prods;

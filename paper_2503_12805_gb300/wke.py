@@ -33,6 +33,9 @@ WKE_NYQ_KEEP = 0
 WKE_NYQ_ZERO = 1
 WKE_ALIAS_CIRCULAR = 0
 WKE_DEALIAS_PAD2 = 1
+WKE_LAYOUT_AUTO = 0
+WKE_LAYOUT_PER_GROUP = 1
+WKE_LAYOUT_SHARED = 2
 WKE_OMEGA_HALF_K2 = 0
 WKE_OMEGA_K2 = 1
 
@@ -47,7 +50,7 @@ class WkeQuadrature(ctypes.Structure):
         ("user_s", C_DOUBLE_P), ("user_sig", C_DOUBLE_P),
         ("R", ctypes.c_double), ("precision", ctypes.c_int), ("nyquist", ctypes.c_int),
         ("dispersion", ctypes.c_int), ("pair_antipodal", ctypes.c_int),
-        ("chunk_bytes", ctypes.c_size_t), ("alias", ctypes.c_int),
+        ("chunk_bytes", ctypes.c_size_t), ("alias", ctypes.c_int), ("layout", ctypes.c_int),
     ]
 
 
@@ -74,7 +77,8 @@ class WkePlanInfo(ctypes.Structure):
         ("products_per_group", ctypes.c_int), ("groups_per_chunk", ctypes.c_int),
         ("n_chunks", ctypes.c_int), ("launches_per_collision", ctypes.c_int),
         ("flops_per_collision", ctypes.c_double), ("l2_bytes_per_collision", ctypes.c_double),
-        ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int),
+        ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int), ("shared_fields", ctypes.c_int),
+        ("units_per_collision", ctypes.c_int),
     ]
 
 
@@ -86,7 +90,7 @@ EXPORTED = [
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
     "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
 ]
-PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist")
+PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist", "axis0")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -337,7 +341,7 @@ class Plan:
                  sphere: str | None = None, sphere_sig: str | None = None, R: float = 0.0,
                  precision: str = "fp64", nyquist: str = "keep", pair_antipodal: bool = True,
                  chunk_bytes: int = 0, dispersion: str = "half_k2", user_s=None, user_sig=None,
-                 dealias: bool = False):
+                 dealias: bool = False, layout: str = "auto"):
         import numpy as np
         q = wke_quadrature_default()
         q.n_r, q.n_s, q.n_sig = n_r, n_s, n_sig
@@ -362,6 +366,7 @@ class Plan:
         q.pair_antipodal = int(pair_antipodal)
         q.chunk_bytes = chunk_bytes
         q.alias = WKE_DEALIAS_PAD2 if dealias else WKE_ALIAS_CIRCULAR
+        q.layout = {"auto": WKE_LAYOUT_AUTO, "per_group": WKE_LAYOUT_PER_GROUP, "shared": WKE_LAYOUT_SHARED}[layout]
         self.d, self.N, self.L = d, N, L
         self.M = n_r * n_s * n_sig
         self.precision = precision

@@ -51,9 +51,10 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("layout", ["per_group", "shared"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_full_field_parity(case, prec):
+def test_full_field_parity(case, prec, layout):
     torch = require_cuda()
     from paper_2503_12805_gb300 import wke
     name, d, N, n_r, n_s, n_sig, sph, sph_sig, gen = case
@@ -61,7 +62,8 @@ def test_full_field_parity(case, prec):
     f = gen()
     quad = _oracle_quad(d, L, n_r, n_s, n_sig, sph, sph_sig)
     ref = O.collision_fast(f, L, quad, return_complex=True)
-    with _plan(wke, d, N, L, n_r, n_s, n_sig, sph, sph_sig, precision=prec) as plan:
+    with _plan(wke, d, N, L, n_r, n_s, n_sig, sph, sph_sig, precision=prec, layout=layout) as plan:
+        assert plan.info().shared_fields == (layout == "shared")
         Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
     scale = np.max(np.abs(ref))
     tol = TOL[prec] if prec == "fp64" else fp32_tolerance(f, L, quad)
@@ -195,6 +197,26 @@ def test_vanishing_nodes_dropped_only_where_exactly_zero():
         scale = np.max(np.abs(ref))
         assert rel_max_err(Q, ref.real, scale) <= 1e-12, kw
         assert rel_max_err(Qim, ref.imag, scale) <= 1e-12, kw
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shared_and_per_group_layouts_agree_at_3d_n64(prec):
+    """The benchmark's rule at 3D N=64 on two radii: each distinct shifted
+    field transformed once per chunk (26 of the 56 the per-group layout
+    transforms per radius) gives the same Q."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    f = I.ring(3, 64, 8.0)
+    out = {}
+    for layout in ("shared", "per_group"):
+        with _plan(wke, 3, 64, 8.0, 2, 8, 8, "cube", precision=prec, layout=layout) as plan:
+            info = plan.info()
+            out[layout] = (gpu_collision(torch, plan, f), info.units_per_collision)
+    assert out["per_group"][1] == 2 * (4 + 8 * 3)
+    # FP32: one radius per chunk, 26 fields in 13 units; FP64: 13 units of a
+    # radius exceed the 48 MiB chunk budget, so radii split and share less
+    assert out["shared"][1] == 2 * 13 if prec == "fp32" else out["shared"][1] < out["per_group"][1]
+    assert rel_max_err(out["shared"][0], out["per_group"][0]) <= TOL[prec]
 
 
 def test_deterministic_repeat():
