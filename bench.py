@@ -247,17 +247,26 @@ def run_gpu(args, rank, world, pool, workers):
     dom = max(classes, key=lambda c: classes[c][0])
     dom_ms, dom_n = classes[dom]
     per_launch_ms = dom_ms / dom_n
-    flops_launch = kernel_flops(dom, info)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
-                "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
-                "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
-                "per_launch_ms": round(per_launch_ms, 5), "launches": dom_n,
-                "kernel_share": {c: round(v[0] / sum(x[0] for x in classes.values()), 4)
-                                 for c, v in classes.items()}}
+    share = {c: round(v[0] / sum(x[0] for x in classes.values()), 4) for c, v in classes.items()}
+    if info.shared_fields and dom == "pass2":
+        # the product pass streams the chunk's transformed units: bytes against the copy bandwidth
+        hbm = peaks.get("hbm_gbs")
+        achieved = kernel_bytes(dom, info) / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "products", "achieved": round(achieved, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if hbm else None,
+                    "traffic": None,
+                    "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)" if hbm else "absent",
+                    "algorithmic_bytes_per_launch": round(kernel_bytes(dom, info)),
+                    "alu_frac": round(kernel_flops(dom, info) / (per_launch_ms * 1e-3) / 1e12 / alu_peak, 4)}
+    else:
+        achieved = kernel_flops(dom, info) / (per_launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                    "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
+                    "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
+    roofline.update({"per_launch_ms": round(per_launch_ms, 5), "launches": dom_n, "kernel_share": share})
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -297,22 +306,45 @@ def kernel_flops(cls, info):
     """Algorithmic flops of one launch of a kernel class (the arithmetic the
     executed algorithm needs: 5 n log2 n per complex n-point transform, 16 per
     point for the two phase products and the packing of a unit, 30 per point
-    per product).  A unit is two shifted fields packed in one transform."""
-    d, N, G = info.d, info.N_compute, info.groups_per_chunk
+    per product in the fused pass 2; in the product pass of the shared-field
+    layout 12 per unit for the unpacking, 9 per group for s and cf, 17 per
+    product).  A unit is two shifted fields packed in one transform; launch
+    counts are averages over the evaluation's chunks."""
+    d, N = info.d, info.N_compute
     nd = N ** d
     P = nd // N
     ppg = info.products_per_group
-    units = (G + 1) // 2 + G * ppg
+    if info.shared_fields:
+        units = info.units_per_collision / info.n_chunks
+        groups = info.n_groups / info.n_chunks
+    else:
+        G = info.groups_per_chunk
+        units = (G + 1) // 2 + G * ppg
+        groups = G
     if cls == "pass1":
         return units * N * (5.0 * P * math.log2(P) + 16.0 * P)
+    if cls == "axis0":
+        return units * P * 5.0 * N * math.log2(N)
     if cls == "pass2":
+        if info.shared_fields:
+            return nd * (12.0 * units + groups * (9.0 + 17.0 * ppg))
         per_group = (1 + ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
-        return G * per_group
+        return groups * per_group
     if cls == "nyquist":   # a chunk's units, two fields per transform
         return units * d * 5.0 * P * math.log2(P)
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
-    return 2.0 * G * nd
+    return 2.0 * groups * nd
+
+
+def kernel_bytes(cls, info, cxb=8, tb=4):
+    """Algorithmic bytes of one launch of the product pass (shared-field
+    layout): every unit of the chunk read once (complex), its d Nyquist
+    tables read once, f read, the FP64 accumulator read and written."""
+    d, N = info.d, info.N_compute
+    nd = N ** d
+    units = info.units_per_collision / info.n_chunks
+    return units * nd * cxb + units * d * (nd // N) * cxb + nd * tb + 2 * nd * 8
 
 
 # ------------------------------------------------------------------ de-aliased variant

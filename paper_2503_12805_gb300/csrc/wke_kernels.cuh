@@ -671,10 +671,17 @@ k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
 // Nyquist imaginary parts) into this thread's column of shared memory; then
 // every group g of the chunk adds, with s = C + F and cf = C F,
 //   sum_p W_p Re[(A_p B_p) s - cf (A_p + B_p)]   (and Im on request).
-// The group sums are added in T with compensation (Neumaier) and the chunk's
-// total goes to the single FP64 accumulator: one addition per point per
-// chunk, in chunk order, so the result is deterministic.
+// The chunk's product table (field slots and weights) is copied to shared
+// memory once per block.  The group sums are added in T with compensation
+// (Neumaier) and the chunk's total goes to the single FP64 accumulator: one
+// addition per point per chunk, in chunk order, so the result is
+// deterministic.
 constexpr int kProductThreads = 128;
+
+template <typename T> struct ProdEntry {
+    int a, b;       // field slots (field id * blockDim)
+    T w;
+};
 
 template <typename T, bool IM, bool NYQ>
 __global__ void __launch_bounds__(kProductThreads)
@@ -683,30 +690,49 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
            const int *__restrict__ prod_local, const double *__restrict__ prod_W, int d, int N, int P,
            int g0, int ng, int K, int PPG) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *fb = reinterpret_cast<cx<T> *>(smem_raw) + threadIdx.x;   // field k at fb[k * blockDim.x]
     const int stride = blockDim.x;
+    cx<T> *fbase = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *fb = fbase + threadIdx.x;          // field k at fb[k * stride]
+    ProdEntry<T> *ptab = reinterpret_cast<ProdEntry<T> *>(fbase + (size_t)K * stride);
+    int *ctab = reinterpret_cast<int *>(ptab + ng * PPG);
+    for (int i = threadIdx.x; i < ng * PPG; i += stride) {
+        const int slot = g0 * PPG + i;
+        ptab[i] = ProdEntry<T>{prod_local[2 * slot] * stride, prod_local[2 * slot + 1] * stride, (T)prod_W[slot]};
+    }
+    for (int i = threadIdx.x; i < ng; i += stride) ctab[i] = group_cfield[g0 + i] * stride;
+    __syncthreads();
     const size_t ND = (size_t)N * P;
     const size_t VS = (size_t)d * P;          // Nyquist table entries per unit
     const int U = (K + 1) / 2;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < ND; idx += (size_t)gridDim.x * blockDim.x) {
         const int i1 = (int)(idx / P), col = (int)(idx - (size_t)i1 * P);
         const T sgn1 = (i1 & 1) ? (T)-1 : (T)1;
-        for (int u = 0; u < U; ++u) {
-            const cx<T> Z = H[(size_t)u * ND + idx];
+        // offsets and signs of this point's table entries (three in 3D, two in 2D)
+        int o1, o2 = 0;
+        T s1, s2 = (T)0;
+        if (d == 3) {
+            const int i2 = col / N, i3 = col - i2 * N;
+            o1 = N * N + i1 * N + i3;
+            o2 = 2 * N * N + i1 * N + i2;
+            s1 = (i2 & 1) ? (T)-1 : (T)1;
+            s2 = (i3 & 1) ? (T)-1 : (T)1;
+        } else {
+            o1 = N + i1;
+            s1 = (col & 1) ? (T)-1 : (T)1;
+        }
+        const cx<T> *Hp = H + idx;
+        const cx<T> *Vu = Vtab;
+        for (int u = 0; u < U; ++u, Hp += ND, Vu += VS) {
+            const cx<T> Z = *Hp;
             T a = (T)0, b = (T)0;
             if (NYQ) {
-                const cx<T> *Vu = Vtab + (size_t)u * VS;
+                const cx<T> v0 = Vu[col], v1 = Vu[o1];
+                a = sgn1 * v0.x + s1 * v1.x;
+                b = sgn1 * v0.y + s1 * v1.y;
                 if (d == 3) {
-                    const int i2 = col / N, i3 = col - i2 * N;
-                    const T sg2 = (i2 & 1) ? (T)-1 : (T)1, sg3 = (i3 & 1) ? (T)-1 : (T)1;
-                    const cx<T> v0 = Vu[col], v1 = Vu[N * N + i1 * N + i3], v2 = Vu[2 * N * N + i1 * N + i2];
-                    a = sgn1 * v0.x + sg2 * v1.x + sg3 * v2.x;
-                    b = sgn1 * v0.y + sg2 * v1.y + sg3 * v2.y;
-                } else {
-                    const T sg2 = (col & 1) ? (T)-1 : (T)1;
-                    const cx<T> v0 = Vu[col], v1 = Vu[N + i1];
-                    a = sgn1 * v0.x + sg2 * v1.x;
-                    b = sgn1 * v0.y + sg2 * v1.y;
+                    const cx<T> v2 = Vu[o2];
+                    a += s2 * v2.x;
+                    b += s2 * v2.y;
                 }
             }
             fb[(2 * u) * stride] = mkc<T>(Z.x + b, a);
@@ -714,18 +740,18 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
         }
         const T F = f[idx];
         T sum = (T)0, comp = (T)0, sumi = (T)0, compi = (T)0;
-        for (int g = g0; g < g0 + ng; ++g) {
-            const cx<T> C = fb[group_cfield[g] * stride];
+        const ProdEntry<T> *pe = ptab;
+        for (int g = 0; g < ng; ++g) {
+            const cx<T> C = fb[ctab[g]];
             const T sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
             T acc = (T)0, acci = (T)0;
-            for (int p = 0; p < PPG; ++p) {
-                const int slot = g * PPG + p;
-                const T W = (T)prod_W[slot];
-                const cx<T> A = fb[prod_local[2 * slot] * stride], B = fb[prod_local[2 * slot + 1] * stride];
+            for (int p = 0; p < PPG; ++p, ++pe) {
+                const ProdEntry<T> e = *pe;
+                const cx<T> A = fb[e.a], B = fb[e.b];
                 const T pr = A.x * B.x - A.y * B.y, pim = A.x * B.y + A.y * B.x;   // A B
                 const T ur = A.x + B.x, ui = A.y + B.y;                            // A + B
-                acc += W * ((pr * sr - pim * si) - (cr * ur - ci * ui));
-                if (IM) acci += W * ((pr * si + pim * sr) - (cr * ui + ci * ur));
+                acc += e.w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
+                if (IM) acci += e.w * ((pr * si + pim * sr) - (cr * ui + ci * ur));
             }
             // Neumaier summation of the group sums
             T tsum = sum + acc;

@@ -186,7 +186,8 @@ static int products_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStre
     const ChunkRange cr = chunk_range(hp, c);
     const int P = cols_of(hp);
     const size_t ND = nd_of(hp);
-    const size_t smem = (size_t)cr.sK * kProductThreads * sizeof(cx<T>);
+    const size_t smem = (size_t)cr.sK * kProductThreads * sizeof(cx<T>) +
+                        (size_t)cr.ng * hp.products_per_group * sizeof(ProdEntry<T>) + (size_t)cr.ng * sizeof(int);
     int rc = 0;
     if ((rc = set_smem(k_products<T, IM, NYQ>, smem))) return rc;
     const int blocks = (int)std::min<size_t>((ND + kProductThreads - 1) / kProductThreads, 152 * 16);
