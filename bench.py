@@ -256,7 +256,7 @@ def run_gpu(args, rank, world, pool, workers):
         achieved = kernel_bytes(dom, info) / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "products", "achieved": round(achieved, 1),
                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if hbm else None,
-                    "traffic": None,
+                    "traffic": PRODUCTS_DRAM_BYTES_3D_N64 if (info.d, info.N_compute) == (3, 64) else None,
                     "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)" if hbm else "absent",
                     "algorithmic_bytes_per_launch": round(kernel_bytes(dom, info)),
                     "alu_frac": round(kernel_flops(dom, info) / (per_launch_ms * 1e-3) / 1e12 / alu_peak, 4)}
@@ -335,6 +335,13 @@ def kernel_flops(cls, info):
     if cls == "forward":
         return 5.0 * nd * math.log2(nd)
     return 2.0 * groups * nd
+
+
+# DRAM bytes (read + write) of one product-pass launch at 3D N=64, M=2048,
+# FP32, warm L2, from an ncu capture of this kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); reported as the roofline's measured traffic for
+# that workload only.
+PRODUCTS_DRAM_BYTES_3D_N64 = 2304 + 9472
 
 
 def kernel_bytes(cls, info, cxb=8, tb=4):
