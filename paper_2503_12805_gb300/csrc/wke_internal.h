@@ -74,7 +74,7 @@ struct HostPlan {
 
     // Launch layout (wke_plan_set_tuning / wke_plan_autotune).
     int tune_p2_points = 8;              // pass-2 points per thread (4 or 8; N >= 128 uses 8)
-    int tune_p1_units_per_block = 0;     // pass-1 units per block (0 = automatic: 3)
+    int tune_p1_units_per_block = 0;     // pass-1 units per block (0 = automatic: 2 shared, 3 per-group)
 };
 
 // Validate arguments and fill `hp` (no device work).  Returns WKE_OK or an

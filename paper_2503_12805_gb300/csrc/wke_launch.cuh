@@ -105,7 +105,10 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t 
             const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH + 8 * N) * sizeof(cx<T>);
             if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
             // enough blocks to fill the GPU several times over
-            const int upb = std::min(nunits, hp.tune_p1_units_per_block > 0 ? hp.tune_p1_units_per_block : 3);
+            // automatic: 2 units per block in the shared-field layout (13-unit chunks
+            // at 3D N=64 give 448 blocks), 3 in the per-group layout (18-unit chunks)
+            const int upb = std::min(nunits, hp.tune_p1_units_per_block > 0 ? hp.tune_p1_units_per_block
+                                                                            : (hp.shared ? 2 : 3));
             dim3 grid(N, (nunits + upb - 1) / upb);
             k_pass1_3d<T, N><<<grid, N * Cfg::TPL, smem, s>>>(ghat, ph, H, tw, p.prod_local, g0, ng,
                                                                hp.fields_per_group, hp.products_per_group, nunits, upb,
