@@ -117,6 +117,20 @@ def _oracle_chunk(args):
     return time.perf_counter() - t
 
 
+def replica_rate(t_step_ms, world, device=None):
+    """Whole-job rate of `world` independent replicas (one per GPU, each
+    evaluating its own copy of the workload): the slowest rank's mean step
+    time, taken with a MAX all-reduce, and world * 1000 / t_max evals/s."""
+    t_max = t_step_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_step_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, world * 1000.0 / t_max
+
+
 def cpu_oracle_rate(pool, nodes_per_worker, workers):
     """Evaluations/s of the FP64 oracle on `workers` host processes, from a
     bounded sample: each worker sums `nodes_per_worker` nodes of the workload."""
@@ -212,12 +226,7 @@ def run_gpu(args, rank, world, pool, workers):
         p32.close()
         return line
     t_step = sum(ms32) / len(ms32)
-    t_max = t_step
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * 1000.0 / t_max
+    t_max, value = replica_rate(t_step, world, dev)
 
     # FP64 path on the same GPU (fewer steps: it is far slower)
     p64 = make("fp64")
@@ -499,13 +508,16 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     pool, workers = make_pool()
+    # per-step sample sized so that the whole run stays near two minutes:
+    # one oracle node costs about 0.06 s per process on the GPU machine's host
+    per_step = max(1, min(args.oracle_nodes, int(120.0 / (max(1, args.steps) * 0.06))))
     try:
         rates = []
         t0 = time.perf_counter()
-        for _ in range(args.warmup):
-            cpu_oracle_rate(pool, max(8, args.oracle_nodes // 4), workers)
+        for _ in range(min(args.warmup, 3)):
+            cpu_oracle_rate(pool, max(1, per_step // 2), workers)
         for _ in range(args.steps):
-            rates.append(cpu_oracle_rate(pool, args.oracle_nodes, workers)[0])
+            rates.append(cpu_oracle_rate(pool, per_step, workers)[0])
         wall = time.perf_counter() - t0
     finally:
         pool.close()
@@ -515,7 +527,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config("fp64 (CPU oracle)"),
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
-                             "sample": f"{args.oracle_nodes} nodes per process per step, {workers} spawn "
+                             "sample": f"{per_step} nodes per process per step, {workers} spawn "
                                        f"processes, scaled to full evaluations; {wall:.1f} s wall"},
             "e2e": {"value": round(rate, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
