@@ -499,7 +499,7 @@ def run_serving(n_requests, seed, wke, budget_bytes, max_active):
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "throughput_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2),
             "max_active": max_active, "budget_gib": round(budget_bytes / 2 ** 30, 1),
-            "mix": "2D N in {64,128,256} (M=4N), 3D N in {32,64} (M=32N); steps U{1..20} RK4, dt=1e-3, FP32"}
+            "mix": "2D N in {64,128,256} (M=4N), 3D N in {32,48,64} (M=32N); steps U{1..20} RK4, dt=1e-3, FP32"}
 
 
 # ------------------------------------------------------------------ reference arm
