@@ -120,7 +120,8 @@ typedef struct wke_quadrature {
                                 de-aliased); 0: every node separately, as
                                 Algorithm 1 loops                              */
     size_t chunk_bytes;      /* budget for the per-chunk intermediate fields;
-                                0 => 48 MiB (sized to stay resident in L2)     */
+                                0 => 48 MiB in FP32 (sized to stay resident in
+                                L2), 64 MiB in FP64                            */
     int alias;               /* WKE_ALIAS_CIRCULAR (default) or
                                 WKE_DEALIAS_PAD2                               */
     int layout;              /* WKE_LAYOUT_AUTO (default), _PER_GROUP or
@@ -152,7 +153,7 @@ typedef struct wke_plan_info {
 /* ------------------------------------------------------------ calls */
 
 /* Defaults: 2D mid-point / 3D cube rules, R = 0 (automatic), FP64, Nyquist
- * kept, omega = |k|^2/2, antipodal pairing on, 48 MiB chunks.  n_r, n_s,
+ * kept, omega = |k|^2/2, antipodal pairing on, automatic chunk budget.  n_r, n_s,
  * n_sig are set to 0 and must be filled in.  Returns WKE_ERR_INVALID if q is
  * NULL. */
 int wke_quadrature_default(wke_quadrature *q);

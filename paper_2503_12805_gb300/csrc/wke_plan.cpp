@@ -513,7 +513,10 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     for (int a = 0; a < d; ++a) nd *= (size_t)hp.N;
     // two groups share one C unit, so a group costs products + 1/2 units
     size_t per_pair = (size_t)(2 * hp.products_per_group + 1) * nd * cxb;
-    hp.chunk_bytes = quad->chunk_bytes ? quad->chunk_bytes : (size_t)48 << 20;
+    // default budget: 48 MiB in FP32 (a 3D N=64 radius of 13 units, 27 MB, double-buffered in
+    // L2); 64 MiB in FP64, whose ALU-bound passes gain more from keeping a radius whole (54 MB)
+    // than from L2 residency
+    hp.chunk_bytes = quad->chunk_bytes ? quad->chunk_bytes : (size_t)(hp.precision == WKE_FP64 ? 64 : 48) << 20;
     hp.groups_per_chunk = (int)std::max<size_t>(1, 2 * (hp.chunk_bytes / per_pair));
     hp.groups_per_chunk = std::min(hp.groups_per_chunk, hp.n_groups);
     hp.n_chunks = (hp.n_groups + hp.groups_per_chunk - 1) / hp.groups_per_chunk;

@@ -213,9 +213,7 @@ def test_shared_and_per_group_layouts_agree_at_3d_n64(prec):
             info = plan.info()
             out[layout] = (gpu_collision(torch, plan, f), info.units_per_collision)
     assert out["per_group"][1] == 2 * (4 + 8 * 3)
-    # FP32: one radius per chunk, 26 fields in 13 units; FP64: 13 units of a
-    # radius exceed the 48 MiB chunk budget, so radii split and share less
-    assert out["shared"][1] == 2 * 13 if prec == "fp32" else out["shared"][1] < out["per_group"][1]
+    assert out["shared"][1] == 2 * 13          # one radius per chunk: 26 fields in 13 units
     assert rel_max_err(out["shared"][0], out["per_group"][0]) <= TOL[prec]
 
 
