@@ -678,8 +678,10 @@ k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
 // deterministic.
 constexpr int kProductThreads = 128;
 
-template <typename T> struct ProdEntry {
-    int a, b;       // field slots (field id * blockDim)
+// One product of the chunk's table: the two field slots (field id * blockDim,
+// below 2^16) packed in one word, and the weight.
+template <typename T> struct __align__(2 * sizeof(T)) ProdEntry {
+    unsigned ab;
     T w;
 };
 
@@ -697,7 +699,8 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
     int *ctab = reinterpret_cast<int *>(ptab + ng * PPG);
     for (int i = threadIdx.x; i < ng * PPG; i += stride) {
         const int slot = g0 * PPG + i;
-        ptab[i] = ProdEntry<T>{prod_local[2 * slot] * stride, prod_local[2 * slot + 1] * stride, (T)prod_W[slot]};
+        ptab[i] = ProdEntry<T>{(unsigned)(prod_local[2 * slot] * stride) | ((unsigned)(prod_local[2 * slot + 1] * stride) << 16),
+                               (T)prod_W[slot]};
     }
     for (int i = threadIdx.x; i < ng; i += stride) ctab[i] = group_cfield[g0 + i] * stride;
     __syncthreads();
@@ -747,7 +750,7 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
             T acc = (T)0, acci = (T)0;
             for (int p = 0; p < PPG; ++p, ++pe) {
                 const ProdEntry<T> e = *pe;
-                const cx<T> A = fb[e.a], B = fb[e.b];
+                const cx<T> A = fb[e.ab & 0xffffu], B = fb[e.ab >> 16];
                 const T pr = A.x * B.x - A.y * B.y, pim = A.x * B.y + A.y * B.x;   // A B
                 const T ur = A.x + B.x, ui = A.y + B.y;                            // A + B
                 acc += e.w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
