@@ -238,6 +238,15 @@ def run_gpu(args, rank, world, pool, workers):
     q64 = Q64.cpu().numpy()
     rel_err = float(np.max(np.abs(q32 - q64)) / np.max(np.abs(q64)))
 
+    # split precision: the axis-0 transforms as TF32 tensor-core GEMMs (hi/lo split)
+    psp = make("split")
+    Qsp = torch.empty_like(f32)
+    mssp, _, _ = timed(psp, f32, Qsp, max(3, min(args.steps, 50)), max(1, min(args.warmup, 3)))
+    split = {"evals_per_s": round(1000.0 / (sum(mssp) / len(mssp)), 3),
+             "rel_err_vs_fp64_gpu": float(np.max(np.abs(Qsp.double().cpu().numpy() - q64)) / np.max(np.abs(q64))),
+             "what": "FP32 plan whose axis-0 DFTs run as TF32 mma.sync GEMMs with hi/lo operand splits"}
+    psp.close()
+
     # end to end through the host-buffer call
     fh = torch.tensor(f64, dtype=torch.float32).pin_memory()
     qh = torch.empty_like(fh).pin_memory()
@@ -283,7 +292,7 @@ def run_gpu(args, rank, world, pool, workers):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config("fp32"),
         "parallelism": "replicas" if world > 1 else "single-gpu",
         "fp64_evals_per_s": round(fp64_rate, 4), "speedup_fp32_vs_fp64": round(value / world / fp64_rate, 2),
-        "fp32_rel_err_vs_fp64_gpu": rel_err, "wall_s_timed": round(wall32, 4),
+        "fp32_rel_err_vs_fp64_gpu": rel_err, "split": split, "wall_s_timed": round(wall32, 4),
         "e2e": {"value": round(e2e_rate, 3), "unit": UNIT, "h2d_bytes_per_step": fh.numel() * 4,
                 "d2h_bytes_per_step": qh.numel() * 4},
         "gpu_launches": args.steps * info.launches_per_collision,

@@ -64,6 +64,12 @@ extern "C" {
 #define WKE_FP32  1   /* transforms and products in float, tables computed in
                          double and rounded, forward transform and the sum over
                          quadrature groups in double                           */
+#define WKE_SPLIT 2   /* WKE_FP32 (float data) whose axis-0 transforms run on
+                         the tensor cores: each N-point DFT as a real GEMM in
+                         TF32 with both operands split into a TF32 high part
+                         and a TF32 low part (three products, FP32
+                         accumulation).  Needs the shared-field layout and a
+                         3D transform grid of N = 32 or 64.                    */
 
 #define WKE_NYQ_KEEP  0   /* modes [-N/2, N/2-1]^d as in Eq. (3.1) (default)  */
 #define WKE_NYQ_ZERO  1   /* zero every mode with a component equal to -N/2   */
@@ -107,7 +113,7 @@ typedef struct wke_quadrature {
     const double *user_sig;  /* same for sigma                                 */
     double R;                /* radial cut-off; 0 => R = 4L/(3 + sqrt 2), i.e.
                                 R = 2S with L = (3 + sqrt 2) S / 2 (Step 1)     */
-    int precision;           /* WKE_FP64 or WKE_FP32                           */
+    int precision;           /* WKE_FP64, WKE_FP32 or WKE_SPLIT                */
     int nyquist;             /* WKE_NYQ_KEEP or WKE_NYQ_ZERO                   */
     int dispersion;          /* WKE_OMEGA_HALF_K2 or WKE_OMEGA_K2              */
     int pair_antipodal;      /* 1 (default): when the sigma rule is antipodal

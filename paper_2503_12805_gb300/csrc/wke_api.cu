@@ -521,7 +521,7 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
     info->shared_fields = hp.shared ? 1 : 0;
     info->units_per_collision = (int)total_units(hp);
     info->M = hp.M;
-    info->precision = hp.precision;
+    info->precision = hp.split ? WKE_SPLIT : hp.precision;
     info->n_groups = hp.n_groups;
     info->fields_per_group = hp.fields_per_group;
     info->products_per_group = hp.products_per_group;

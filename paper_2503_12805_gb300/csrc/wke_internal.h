@@ -22,6 +22,9 @@ struct HostPlan {
     // only for de-aliased plans (N = 2 N_in, zero padding).
     int N_in = 0;
     bool dealias = false;
+    // WKE_SPLIT: precision is WKE_FP32 (float data) and the axis-0
+    // transforms use the tensor-core DFT
+    bool split = false;
     double L = 0, R = 0;
     int n_r = 0, n_s = 0, n_sig = 0;
     int precision = WKE_FP64, nyquist = WKE_NYQ_KEEP, dispersion = WKE_OMEGA_HALF_K2;

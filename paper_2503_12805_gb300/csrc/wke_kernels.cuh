@@ -665,6 +665,101 @@ k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
     for (int e = 0; e < E; ++e) Hu[(size_t)(t + e * TPL) * P] = v[e];
 }
 
+// Split-precision axis-0 transform on the tensor cores (WKE_SPLIT).  The
+// inverse N-point DFT of every column of a tile of CB = 32 columns is the
+// real GEMM
+//   [Re Z; Im Z] = [[Re F, -Im F], [Im F, Re F]] [Re H; Im H],
+//   F[i1][j1] = exp(+2 pi i i1 j1 / N)            (2N x 2N times 2N x 32),
+// computed with mma.sync m16n8k8 in TF32.  Each operand x is split into
+// x_hi = x rounded to TF32 and x_lo = (x - x_hi) rounded to TF32, and
+// A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is below
+// 2^-22 |A| |B|), each 8-wide k-step on the tensor cores and the 2N / 8 step
+// sums added in FP32.  The F entries come from the
+// twiddle table.  Warp w owns output rows 16 w .. 16 w + 15 of Re Z and of
+// Im Z, so each thread holds the real and imaginary parts of the same points.
+// mma.sync m16n8k8 fragments (g = lane / 4, q = lane % 4): A a0 (g, q),
+// a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4); B b0 (k = q, n = g),
+// b1 (q + 4, g); C c0 (g, 2q), c1 (g, 2q + 1), c2 (g + 8, 2q), c3 (g + 8, 2q + 1).
+__device__ __forceinline__ unsigned tf32_round(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
+    hi = tf32_round(x);
+    lo = tf32_round(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int N>
+__global__ void __launch_bounds__(N / 16 * 32)
+k_axis0_tc(float2 *__restrict__ H, const float2 *__restrict__ tw_g, int P) {
+    constexpr int CB = 32, K = 2 * N, LD = CB + 8;   // LD: conflict-free B fragment reads
+    __shared__ float2 tw[N];
+    __shared__ float Bs[K * LD];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    float2 *Hu = H + (size_t)blockIdx.y * N * P + (size_t)blockIdx.x * CB;
+    for (int i = threadIdx.x; i < N * CB; i += blockDim.x) {
+        const int j1 = i / CB, c = i - j1 * CB;
+        const float2 h = Hu[(size_t)j1 * P + c];
+        Bs[j1 * LD + c] = h.x;
+        Bs[(N + j1) * LD + c] = h.y;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[t][nt][e] = 0.0f;
+    for (int kk = 0; kk < K / 8; ++kk) {
+        unsigned ahi[2][4], alo[2][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i1 = 16 * warp + g + ((e & 1) ? 8 : 0);
+            const int k = 8 * kk + q + ((e & 2) ? 4 : 0);
+            const int half = k >= N, j1 = half ? k - N : k;
+            const float2 w = tw[(i1 * j1) & (N - 1)];
+            // row of Re Z: (Re F, -Im F); row of Im Z: (Im F, Re F)
+            tf32_split(half ? -w.y : w.x, ahi[0][e], alo[0][e]);
+            tf32_split(half ? w.x : w.y, ahi[1][e], alo[1][e]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            unsigned bhi0, blo0, bhi1, blo1;
+            tf32_split(Bs[(8 * kk + q) * LD + 8 * nt + g], bhi0, blo0);
+            tf32_split(Bs[(8 * kk + q + 4) * LD + 8 * nt + g], bhi1, blo1);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                // each 8-wide k-step sums into a fresh fragment, added to the
+                // running sum with a rounded FP32 addition (the tensor cores'
+                // own accumulation over all 2N terms loses more)
+                float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                mma_tf32(part, alo[t], bhi0, bhi1);
+                mma_tf32(part, ahi[t], blo0, blo1);
+                mma_tf32(part, ahi[t], bhi0, bhi1);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[t][nt][e] += part[e];
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i1 = 16 * warp + g + ((e & 2) ? 8 : 0);
+            const int c = 8 * nt + 2 * q + (e & 1);
+            Hu[(size_t)i1 * P + c] = make_float2(acc[0][nt][e], acc[1][nt][e]);
+        }
+}
+
 // Product pass: one grid point per thread and loop.  The chunk's K fields at
 // the point are unpacked from the transformed units (real-slot field
 // (Re Z + b) + i a, imaginary-slot field (Im Z - a) + i b, a and b the

@@ -305,7 +305,21 @@ int pass2_T(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_
     return (int)cudaErrorInvalidValue;
 }
 
+template <int N> static int axis0_tc_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    const int P = cols_of(hp);
+    k_axis0_tc<N><<<dim3(P / 32, units_of_chunk(hp, c)), N / 16 * 32, 0, s>>>(
+        static_cast<float2 *>(p.H), static_cast<const float2 *>(p.tw), P);
+    return (int)cudaGetLastError();
+}
+
 template <typename T> int axis0_T(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (hp.split) {
+            if (hp.N == 64) return axis0_tc_n<64>(hp, p, c, s);
+            if (hp.N == 32) return axis0_tc_n<32>(hp, p, c, s);
+            return (int)cudaErrorInvalidValue;
+        }
+    }
     switch (hp.N) {
         case 16: return axis0_n<T, 16>(hp, p, c, s);
         case 32: return axis0_n<T, 32>(hp, p, c, s);

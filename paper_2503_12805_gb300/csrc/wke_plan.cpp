@@ -325,8 +325,10 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
         return fail(WKE_ERR_INVALID, "n_r, n_s and n_sig must be >= 1");
     if ((long long)quad->n_r * quad->n_s * quad->n_sig != (long long)M)
         return fail(WKE_ERR_INVALID, "M must equal n_r * n_s * n_sig");
-    if (quad->precision != WKE_FP64 && quad->precision != WKE_FP32)
-        return fail(WKE_ERR_INVALID, "precision must be WKE_FP64 or WKE_FP32");
+    if (quad->precision != WKE_FP64 && quad->precision != WKE_FP32 && quad->precision != WKE_SPLIT)
+        return fail(WKE_ERR_INVALID, "precision must be WKE_FP64, WKE_FP32 or WKE_SPLIT");
+    if (quad->precision == WKE_SPLIT && quad->layout == WKE_LAYOUT_PER_GROUP)
+        return fail(WKE_ERR_INVALID, "WKE_SPLIT needs the shared-field layout");
     if (quad->nyquist != WKE_NYQ_KEEP && quad->nyquist != WKE_NYQ_ZERO)
         return fail(WKE_ERR_INVALID, "nyquist must be WKE_NYQ_KEEP or WKE_NYQ_ZERO");
     if (quad->dispersion != WKE_OMEGA_HALF_K2 && quad->dispersion != WKE_OMEGA_K2)
@@ -354,7 +356,8 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     hp.n_r = quad->n_r;
     hp.n_s = quad->n_s;
     hp.n_sig = quad->n_sig;
-    hp.precision = quad->precision;
+    hp.split = quad->precision == WKE_SPLIT;
+    hp.precision = hp.split ? WKE_FP32 : quad->precision;
     hp.nyquist = quad->nyquist;
     hp.dispersion = quad->dispersion;
 
@@ -525,9 +528,11 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     if (quad->layout != WKE_LAYOUT_AUTO && quad->layout != WKE_LAYOUT_PER_GROUP && quad->layout != WKE_LAYOUT_SHARED)
         return fail(WKE_ERR_INVALID, "layout must be WKE_LAYOUT_AUTO, _PER_GROUP or _SHARED");
     if (quad->layout != WKE_LAYOUT_PER_GROUP) {
-        int rc2 = build_shared_layout(hp, quad->layout == WKE_LAYOUT_SHARED);
+        int rc2 = build_shared_layout(hp, quad->layout == WKE_LAYOUT_SHARED || hp.split);
         if (rc2) return rc2;
     }
+    if (hp.split && (d != 3 || (hp.N != 32 && hp.N != 64)))
+        return fail(WKE_ERR_UNSUPPORTED, "WKE_SPLIT is built for 3D transform grids of N = 32 or 64");
 
     hp.scale = std::ldexp(1.0, 1 - d) * (hp.dispersion == WKE_OMEGA_K2 ? 0.5 : 1.0);
     return WKE_OK;

@@ -29,6 +29,7 @@ WKE_SPHERE_USER = 3
 
 WKE_FP64 = 0
 WKE_FP32 = 1
+WKE_SPLIT = 2
 WKE_NYQ_KEEP = 0
 WKE_NYQ_ZERO = 1
 WKE_ALIAS_CIRCULAR = 0
@@ -360,7 +361,7 @@ class Plan:
             q.sphere_rule_sig = WKE_SPHERE_USER
             q.user_sig = arr.ctypes.data_as(C_DOUBLE_P)
         q.R = R
-        q.precision = {"fp64": WKE_FP64, "fp32": WKE_FP32}[precision]
+        q.precision = {"fp64": WKE_FP64, "fp32": WKE_FP32, "split": WKE_SPLIT}[precision]
         q.nyquist = {"keep": WKE_NYQ_KEEP, "zero": WKE_NYQ_ZERO}[nyquist]
         q.dispersion = {"half_k2": WKE_OMEGA_HALF_K2, "k2": WKE_OMEGA_K2}[dispersion]
         q.pair_antipodal = int(pair_antipodal)

@@ -106,3 +106,19 @@ def test_dealias_argument_checks_and_footprint(wke):
     q.alias = wke.WKE_ALIAS_CIRCULAR
     circular = wke.wke_plan_footprint_bytes(3, 32, 8.0, 256, q)
     assert dealiased > 4 * circular
+
+
+def test_split_precision_argument_checks(wke):
+    """WKE_SPLIT runs on the shared-field layout with a 3D grid of N = 32 or 64."""
+    size = ctypes.c_size_t()
+    lib = wke.lib()
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = 2, 8, 8
+    q.precision = wke.WKE_SPLIT
+    assert lib.wke_plan_footprint_bytes(3, 64, 8.0, 128, ctypes.byref(q), ctypes.byref(size)) == wke.WKE_OK
+    assert lib.wke_plan_footprint_bytes(3, 48, 8.0, 128, ctypes.byref(q), ctypes.byref(size)) == -4
+    q.n_s, q.n_sig = 4, 4
+    assert lib.wke_plan_footprint_bytes(2, 64, 8.0, 32, ctypes.byref(q), ctypes.byref(size)) == -4
+    q.n_s, q.n_sig = 8, 8
+    q.layout = wke.WKE_LAYOUT_PER_GROUP
+    assert lib.wke_plan_footprint_bytes(3, 64, 8.0, 128, ctypes.byref(q), ctypes.byref(size)) == wke.WKE_ERR_INVALID
