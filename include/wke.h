@@ -193,6 +193,13 @@ int wke_plan_footprint_bytes(int d, int N, double L, int M,
 /* Fill *info for an existing plan. */
 int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info);
 
+/* Fill *info for the plan wke_plan_create would build from these arguments,
+ * without creating it: host work only, no device memory or CUDA call
+ * (device_bytes is the footprint of wke_plan_footprint_bytes).  For
+ * planning and admission; errors as wke_plan_create's argument checks. */
+int wke_plan_describe(int d, int N, double L, int M, const wke_quadrature *quad,
+                      wke_plan_info *info);
+
 /* Copy the node table to host memory: M rows, in (p1, p2, p3) lexicographic
  * order, of 1 + 3d doubles: W_p, q (d), a (d), b (d).  `out_host` must hold
  * M * (1 + 3d) doubles. */

@@ -512,9 +512,8 @@ int wke_plan_destroy(wke_plan *plan) {
     return WKE_OK;
 }
 
-int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
-    if (!plan || !info) return fail(WKE_ERR_INVALID, "plan or info is NULL");
-    const HostPlan &hp = plan->hp;
+// Counts of a plan layout (shared by wke_plan_get_info and wke_plan_describe).
+static void fill_info(const HostPlan &hp, wke_plan_info *info) {
     info->d = hp.d;
     info->N = hp.N_in;
     info->N_compute = hp.N;
@@ -532,7 +531,22 @@ int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
                                    (hp.dealias ? 1 + 2 * hp.d : 0);
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
+}
+
+int wke_plan_get_info(const wke_plan *plan, wke_plan_info *info) {
+    if (!plan || !info) return fail(WKE_ERR_INVALID, "plan or info is NULL");
+    fill_info(plan->hp, info);
     info->device_bytes = plan->bytes;
+    return WKE_OK;
+}
+
+int wke_plan_describe(int d, int N, double L, int M, const wke_quadrature *quad, wke_plan_info *info) {
+    if (!info) return fail(WKE_ERR_INVALID, "info is NULL");
+    HostPlan hp;
+    int rc = build_host_plan(d, N, L, M, quad, hp);
+    if (rc) return rc;
+    fill_info(hp, info);
+    info->device_bytes = plan_device_bytes(hp);
     return WKE_OK;
 }
 

@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_plan_destroy": (i, [vp]),
         "wke_plan_footprint_bytes": (i, [i, i, d, i, QP, ctypes.POINTER(sz)]),
         "wke_plan_get_info": (i, [vp, ctypes.POINTER(WkePlanInfo)]),
+        "wke_plan_describe": (i, [i, i, d, i, QP, ctypes.POINTER(WkePlanInfo)]),
         "wke_plan_node_table": (i, [vp, C_DOUBLE_P]),
         "wke_collision": (i, [vp, vp, vp, vp]),
         "wke_collision_ex": (i, [vp, vp, vp, vp, vp]),
@@ -183,6 +184,12 @@ def wke_plan_footprint_bytes(d: int, N: int, L: float, M: int, quad: WkeQuadratu
 def wke_plan_get_info(plan) -> WkePlanInfo:
     info = WkePlanInfo()
     _check(lib().wke_plan_get_info(plan, ctypes.byref(info)))
+    return info
+
+
+def wke_plan_describe(d: int, N: int, L: float, M: int, quad: WkeQuadrature) -> WkePlanInfo:
+    info = WkePlanInfo()
+    _check(lib().wke_plan_describe(d, N, L, M, ctypes.byref(quad), ctypes.byref(info)))
     return info
 
 

@@ -122,3 +122,42 @@ def test_split_precision_argument_checks(wke):
     q.n_s, q.n_sig = 8, 8
     q.layout = wke.WKE_LAYOUT_PER_GROUP
     assert lib.wke_plan_footprint_bytes(3, 64, 8.0, 128, ctypes.byref(q), ctypes.byref(size)) == wke.WKE_ERR_INVALID
+
+
+def _describe(wke, d, N, nr, ns, nsig, **fields):
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = nr, ns, nsig
+    for k, v in fields.items():
+        setattr(q, k, v)
+    return wke.wke_plan_describe(d, N, 8.0, nr * ns * nsig, q)
+
+
+def test_shared_field_layout_counts(wke):
+    """The shared-field layout on the benchmark rule (3D N=64, 32 x 8 x 8 cube):
+    per radius 26 distinct shifted fields (8 C fields r qhat, 6 edge and 12
+    face-diagonal differences r (qhat - sigma)/2) in 13 units, one radius per
+    chunk, 3 products per group after the vanishing sigma = +-qhat pair;
+    the per-group layout transforms 896 units.  No device work is done."""
+    info = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32)
+    assert info.shared_fields == 1 and info.products_per_group == 3
+    assert info.n_chunks == 32 and info.units_per_collision == 32 * 13
+    assert info.launches_per_collision == 2 + 4 * 32 + 1
+    fp64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP64)
+    assert fp64.units_per_collision == 32 * 13            # a whole radius fits the FP64 budget
+    per_group = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, layout=wke.WKE_LAYOUT_PER_GROUP)
+    assert per_group.shared_fields == 0 and per_group.units_per_collision == 256 * 3 + 128
+    # with the Nyquist modes zeroed F is not the grid interpolant: no product vanishes
+    zero = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, nyquist=wke.WKE_NYQ_ZERO)
+    assert zero.products_per_group == 4
+    # 2D mid-point 4 x 4: 8 distinct fields per radius, 1 product per group
+    two_d = _describe(wke, 2, 128, 32, 4, 4, precision=wke.WKE_FP32)
+    assert two_d.shared_fields == 1 and two_d.products_per_group == 1 and two_d.units_per_collision == 32 * 4
+
+
+def test_describe_matches_footprint_and_rejects_like_create(wke):
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = 4, 8, 8
+    info = wke.wke_plan_describe(3, 32, 8.0, 256, q)
+    assert info.device_bytes == wke.wke_plan_footprint_bytes(3, 32, 8.0, 256, q)
+    info2 = wke.WkePlanInfo()
+    assert wke.lib().wke_plan_describe(3, 128, 8.0, 256, ctypes.byref(q), ctypes.byref(info2)) == -4
