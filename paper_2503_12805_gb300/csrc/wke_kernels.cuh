@@ -780,7 +780,7 @@ template <typename T> struct __align__(2 * sizeof(T)) ProdEntry {
     T w;
 };
 
-template <typename T, bool IM, bool NYQ>
+template <typename T, bool IM, bool NYQ, int PPGC>
 __global__ void __launch_bounds__(kProductThreads)
 k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
            double *__restrict__ Qacc, double *__restrict__ Qim, const int *__restrict__ group_cfield,
@@ -799,17 +799,19 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
     }
     for (int i = threadIdx.x; i < ng; i += stride) ctab[i] = group_cfield[g0 + i] * stride;
     __syncthreads();
-    const size_t ND = (size_t)N * P;
+    // N^d < 2^31 for every compiled length: point indices are 32-bit
+    const unsigned ND = (unsigned)N * (unsigned)P;
     const size_t VS = (size_t)d * P;          // Nyquist table entries per unit
     const int U = (K + 1) / 2;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < ND; idx += (size_t)gridDim.x * blockDim.x) {
-        const int i1 = (int)(idx / P), col = (int)(idx - (size_t)i1 * P);
+    const int ppg = PPGC > 0 ? PPGC : PPG;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ND; idx += gridDim.x * blockDim.x) {
+        const int i1 = (int)(idx / (unsigned)P), col = (int)(idx - (unsigned)i1 * (unsigned)P);
         const T sgn1 = (i1 & 1) ? (T)-1 : (T)1;
         // offsets and signs of this point's table entries (three in 3D, two in 2D)
         int o1, o2 = 0;
         T s1, s2 = (T)0;
         if (d == 3) {
-            const int i2 = col / N, i3 = col - i2 * N;
+            const int i2 = (int)((unsigned)col / (unsigned)N), i3 = col - i2 * N;
             o1 = N * N + i1 * N + i3;
             o2 = 2 * N * N + i1 * N + i2;
             s1 = (i2 & 1) ? (T)-1 : (T)1;
@@ -843,7 +845,8 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
             const cx<T> C = fb[ctab[g]];
             const T sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
             T acc = (T)0, acci = (T)0;
-            for (int p = 0; p < PPG; ++p, ++pe) {
+#pragma unroll
+            for (int p = 0; p < ppg; ++p, ++pe) {
                 const ProdEntry<T> e = *pe;
                 const cx<T> A = fb[e.ab & 0xffffu], B = fb[e.ab >> 16];
                 const T pr = A.x * B.x - A.y * B.y, pim = A.x * B.y + A.y * B.x;   // A B

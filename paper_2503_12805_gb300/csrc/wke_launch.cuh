@@ -184,21 +184,34 @@ template <typename T, int N> static int axis0_n(const HostPlan &hp, const Device
     }
 }
 
-template <typename T, bool IM, bool NYQ>
-static int products_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+template <typename T, bool IM, bool NYQ, int PPGC>
+static int products_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
     const ChunkRange cr = chunk_range(hp, c);
     const int P = cols_of(hp);
     const size_t ND = nd_of(hp);
     const size_t smem = (size_t)cr.sK * kProductThreads * sizeof(cx<T>) +
                         (size_t)cr.ng * hp.products_per_group * sizeof(ProdEntry<T>) + (size_t)cr.ng * sizeof(int);
     int rc = 0;
-    if ((rc = set_smem(k_products<T, IM, NYQ>, smem))) return rc;
+    if ((rc = set_smem(k_products<T, IM, NYQ, PPGC>, smem))) return rc;
     const int blocks = (int)std::min<size_t>((ND + kProductThreads - 1) / kProductThreads, 152 * 16);
-    k_products<T, IM, NYQ><<<blocks, kProductThreads, smem, s>>>(
+    k_products<T, IM, NYQ, PPGC><<<blocks, kProductThreads, smem, s>>>(
         static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
         p.Qacc_im, p.group_cfield, p.prod_local, p.prod_W, hp.d, hp.N, P, cr.g0, cr.ng, cr.sK,
         hp.products_per_group);
     return (int)cudaGetLastError();
+}
+
+// The product count per group is a template constant for the counts the
+// built-in rules give (1 to 4), so that the product loop unrolls.
+template <typename T, bool IM, bool NYQ>
+static int products_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    switch (hp.products_per_group) {
+    case 1: return products_nimp<T, IM, NYQ, 1>(hp, p, c, s);
+    case 2: return products_nimp<T, IM, NYQ, 2>(hp, p, c, s);
+    case 3: return products_nimp<T, IM, NYQ, 3>(hp, p, c, s);
+    case 4: return products_nimp<T, IM, NYQ, 4>(hp, p, c, s);
+    default: return products_nimp<T, IM, NYQ, 0>(hp, p, c, s);
+    }
 }
 
 template <typename T>
