@@ -43,6 +43,11 @@ template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T> *dst, co
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
+// 16 bytes global -> shared, both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
@@ -772,6 +777,8 @@ k_axis0_tc(float2 *__restrict__ H, const float2 *__restrict__ tw_g, int P) {
 // addition per point per chunk, in chunk order, so the result is
 // deterministic.
 constexpr int kProductThreads = 128;
+// dynamic shared memory a block may opt in to (227 KB)
+constexpr size_t kMaxDynamicSmem = 227 * 1024;
 
 // One product of the chunk's table: the two field slots (field id * blockDim,
 // below 2^16) packed in one word, and the weight.
@@ -867,6 +874,129 @@ k_products(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T 
         Qacc[idx] += (double)sum + (double)comp;
         if (IM) Qim[idx] += (double)sumi + (double)compi;
     }
+}
+
+// Product pass with staged inputs (3D, and 2D rows of at least a block).
+// Block b holds the kProductThreads consecutive points p0 = b kProductThreads,
+// ... of one i1 row (P is a multiple of the block).  Before any arithmetic the
+// block issues, all at once with cp.async, the copies of each unit's packed
+// values at its points (into field slot 2u), of the unit's V_0 entries at its
+// columns (slot 2u + 1) and of the other tables' entries its points use (a
+// table area of TS entries per unit: in 3D the row V_1(i1, .) and the W2
+// entries V_2(i1, i2lo ..), in 2D V_1(i1)); the unit loop and the products
+// then read shared memory only.  Same arithmetic, in the same order, as
+// k_products.
+template <typename T, bool IM, bool NYQ, int PPGC>
+__global__ void __launch_bounds__(kProductThreads)
+k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, const T *__restrict__ f,
+                  double *__restrict__ Qacc, double *__restrict__ Qim, const int *__restrict__ group_cfield,
+                  const int *__restrict__ prod_local, const double *__restrict__ prod_W, int d, int N, int P,
+                  int g0, int ng, int K, int PPG, int TS, int W2) {
+    constexpr int B = kProductThreads;
+    constexpr int PER16 = 16 / (int)sizeof(cx<T>);   // entries per 16-byte copy
+    constexpr int PIECES = B / PER16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int U = (K + 1) / 2;
+    cx<T> *fbase = reinterpret_cast<cx<T> *>(smem_raw);   // 2U slots of B points
+    cx<T> *tabs = fbase + (size_t)2 * U * B;
+    ProdEntry<T> *ptab = reinterpret_cast<ProdEntry<T> *>(tabs + (NYQ ? (size_t)U * TS : 0));
+    int *ctab = reinterpret_cast<int *>(ptab + ng * PPG);
+    const unsigned ND = (unsigned)N * (unsigned)P;
+    const unsigned p0 = blockIdx.x * B;
+    const int i1 = (int)(p0 / (unsigned)P), col0 = (int)(p0 - (unsigned)i1 * (unsigned)P);
+    const int i2lo = col0 / N;
+    const size_t VS = (size_t)d * P;          // Nyquist table entries per unit
+    for (int i = threadIdx.x; i < U * PIECES; i += B) {
+        const int u = i / PIECES, k = (i - u * PIECES) * PER16;
+        cp_async16(fbase + (size_t)(2 * u) * B + k, H + (size_t)u * ND + p0 + k);
+        if (NYQ) cp_async16(fbase + (size_t)(2 * u + 1) * B + k, Vtab + (size_t)u * VS + col0 + k);
+    }
+    if (NYQ && d == 3) {
+        const int RP = N / PER16;
+        for (int i = threadIdx.x; i < U * RP; i += B) {
+            const int u = i / RP, k = (i - u * RP) * PER16;
+            cp_async16(tabs + (size_t)u * TS + k, Vtab + (size_t)u * VS + (size_t)P + (size_t)i1 * N + k);
+        }
+        const int n2 = min(W2, N - i2lo);
+        for (int i = threadIdx.x; i < U * n2; i += B) {
+            const int u = i / n2, k = i - u * n2;
+            cp_async_cx<T>(tabs + (size_t)u * TS + N + k,
+                           Vtab + (size_t)u * VS + (size_t)2 * P + (size_t)i1 * N + i2lo + k);
+        }
+    } else if (NYQ) {
+        for (int u = threadIdx.x; u < U; u += B) cp_async_cx<T>(tabs + (size_t)u * TS, Vtab + (size_t)u * VS + N + i1);
+    }
+    cp_async_commit();
+    for (int i = threadIdx.x; i < ng * PPG; i += B) {
+        const int slot = g0 * PPG + i;
+        ptab[i] = ProdEntry<T>{(unsigned)(prod_local[2 * slot] * B) | ((unsigned)(prod_local[2 * slot + 1] * B) << 16),
+                               (T)prod_W[slot]};
+    }
+    for (int i = threadIdx.x; i < ng; i += B) ctab[i] = group_cfield[g0 + i] * B;
+    cp_async_wait<0>();
+    __syncthreads();
+    const int ppg = PPGC > 0 ? PPGC : PPG;
+    const int col = col0 + threadIdx.x;
+    // this point's table offsets and signs: 3D V_1 at i3 (sign (-1)^{i2}) and
+    // V_2 at i2 (sign (-1)^{i3}); 2D V_1 (sign (-1)^{col})
+    int o1 = 0, o2 = 0;
+    T s1, s2 = (T)0;
+    if (d == 3) {
+        const int i2 = col / N, i3 = col - i2 * N;
+        o1 = i3;
+        o2 = N + i2 - i2lo;
+        s1 = (i2 & 1) ? (T)-1 : (T)1;
+        s2 = (i3 & 1) ? (T)-1 : (T)1;
+    } else {
+        s1 = (col & 1) ? (T)-1 : (T)1;
+    }
+    const T sgn1 = (i1 & 1) ? (T)-1 : (T)1;
+    cx<T> *fb = fbase + threadIdx.x;
+    const cx<T> *tv = tabs;
+    for (int u = 0; u < U; ++u, tv += TS) {
+        const cx<T> Z = fb[(2 * u) * B];
+        T a = (T)0, b = (T)0;
+        if (NYQ) {
+            const cx<T> v0 = fb[(2 * u + 1) * B], v1 = tv[o1];
+            a = sgn1 * v0.x + s1 * v1.x;
+            b = sgn1 * v0.y + s1 * v1.y;
+            if (d == 3) {
+                const cx<T> v2 = tv[o2];
+                a += s2 * v2.x;
+                b += s2 * v2.y;
+            }
+        }
+        fb[(2 * u) * B] = mkc<T>(Z.x + b, a);
+        if (2 * u + 1 < K) fb[(2 * u + 1) * B] = mkc<T>(Z.y - a, b);
+    }
+    const unsigned idx = p0 + threadIdx.x;
+    const T F = f[idx];
+    T sum = (T)0, comp = (T)0, sumi = (T)0, compi = (T)0;
+    const ProdEntry<T> *pe = ptab;
+    for (int g = 0; g < ng; ++g) {
+        const cx<T> C = fb[ctab[g]];
+        const T sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
+        T acc = (T)0, acci = (T)0;
+#pragma unroll
+        for (int p = 0; p < ppg; ++p, ++pe) {
+            const ProdEntry<T> e = *pe;
+            const cx<T> A = fb[e.ab & 0xffffu], Bf = fb[e.ab >> 16];
+            const T pr = A.x * Bf.x - A.y * Bf.y, pim = A.x * Bf.y + A.y * Bf.x;   // A B
+            const T ur = A.x + Bf.x, ui = A.y + Bf.y;                              // A + B
+            acc += e.w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
+            if (IM) acci += e.w * ((pr * si + pim * sr) - (cr * ui + ci * ur));
+        }
+        T tsum = sum + acc;
+        comp += fabs(sum) >= fabs(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+        sum = tsum;
+        if (IM) {
+            tsum = sumi + acci;
+            compi += fabs(sumi) >= fabs(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+            sumi = tsum;
+        }
+    }
+    Qacc[idx] += (double)sum + (double)comp;
+    if (IM) Qim[idx] += (double)sumi + (double)compi;
 }
 
 // ------------------------------------------------------------------ finalize

@@ -189,6 +189,27 @@ static int products_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStr
     const ChunkRange cr = chunk_range(hp, c);
     const int P = cols_of(hp);
     const size_t ND = nd_of(hp);
+    if (P % kProductThreads == 0) {
+        // staged kernel (3D, and 2D rows of at least a block), when its shared memory fits
+        const int U = (cr.sK + 1) / 2;
+        int W2 = 0, TS = 2;                   // 2D: one V_1 entry per unit (two keep 16-byte alignment)
+        if (hp.d == 3) {
+            W2 = kProductThreads / hp.N + 2;  // V_2 entries a block's columns use, at most
+            W2 += (hp.N + W2) & 1;            // keeps each unit's table 16-byte aligned
+            TS = hp.N + W2;
+        }
+        const size_t smem3 = ((size_t)2 * U * kProductThreads + (NYQ ? (size_t)U * TS : 0)) * sizeof(cx<T>) +
+                             (size_t)cr.ng * hp.products_per_group * sizeof(ProdEntry<T>) + (size_t)cr.ng * sizeof(int);
+        if (smem3 <= kMaxDynamicSmem) {
+            int rc = 0;
+            if ((rc = set_smem(k_products_staged<T, IM, NYQ, PPGC>, smem3))) return rc;
+            k_products_staged<T, IM, NYQ, PPGC><<<(unsigned)(ND / kProductThreads), kProductThreads, smem3, s>>>(
+                static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
+                p.Qacc_im, p.group_cfield, p.prod_local, p.prod_W, hp.d, hp.N, P, cr.g0, cr.ng, cr.sK,
+                hp.products_per_group, TS, W2);
+            return (int)cudaGetLastError();
+        }
+    }
     const size_t smem = (size_t)cr.sK * kProductThreads * sizeof(cx<T>) +
                         (size_t)cr.ng * hp.products_per_group * sizeof(ProdEntry<T>) + (size_t)cr.ng * sizeof(int);
     int rc = 0;
