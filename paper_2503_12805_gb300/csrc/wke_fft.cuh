@@ -38,6 +38,28 @@ template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { 
 template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
     return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// FP32: the two lanes of a complex sum in one packed f32x2 instruction
+// (each lane rounded as a scalar add).
+__device__ __forceinline__ unsigned long long pack2(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+template <> __device__ __forceinline__ float2 cadd<float>(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
+template <> __device__ __forceinline__ float2 csub<float>(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
 template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
 // multiply by DIR * i
 template <typename T, int DIR> __device__ __forceinline__ cx<T> mul_i(cx<T> a) {

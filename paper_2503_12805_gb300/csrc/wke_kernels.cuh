@@ -982,7 +982,8 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
             const ProdEntry<T> e = *pe;
             const cx<T> A = fb[e.ab & 0xffffu], Bf = fb[e.ab >> 16];
             const T pr = A.x * Bf.x - A.y * Bf.y, pim = A.x * Bf.y + A.y * Bf.x;   // A B
-            const T ur = A.x + Bf.x, ui = A.y + Bf.y;                              // A + B
+            const cx<T> Sab = cadd<T>(A, Bf);                                      // A + B
+            const T ur = Sab.x, ui = Sab.y;
             acc += e.w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
             if (IM) acci += e.w * ((pr * si + pim * sr) - (cr * ui + ci * ur));
         }
