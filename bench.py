@@ -359,7 +359,7 @@ def kernel_flops(cls, info):
 # FP32, warm L2, from an ncu capture of this kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); reported as the roofline's measured traffic for
 # that workload only.
-PRODUCTS_DRAM_BYTES_3D_N64 = 6400 + 40448
+PRODUCTS_DRAM_BYTES_3D_N64 = 4608 + 37120
 
 
 def kernel_bytes(cls, info, cxb=8, tb=4):

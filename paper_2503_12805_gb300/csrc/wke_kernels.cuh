@@ -906,23 +906,38 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
     const int i1 = (int)(p0 / (unsigned)P), col0 = (int)(p0 - (unsigned)i1 * (unsigned)P);
     const int i2lo = col0 / N;
     const size_t VS = (size_t)d * P;          // Nyquist table entries per unit
-    for (int i = threadIdx.x; i < U * PIECES; i += B) {
-        const int u = i / PIECES, k = (i - u * PIECES) * PER16;
-        cp_async16(fbase + (size_t)(2 * u) * B + k, H + (size_t)u * ND + p0 + k);
-        if (NYQ) cp_async16(fbase + (size_t)(2 * u + 1) * B + k, Vtab + (size_t)u * VS + col0 + k);
+    // each thread walks (unit u, piece k) of its copies as i = tid, tid + B, ...
+    // with (u, k) = (i / R, i % R) stepped by (B / R, B % R): no division per copy
+    auto walk = [](int U_, int R, auto &&copy) {
+        int u = (int)threadIdx.x / R, k = (int)threadIdx.x - u * R;
+        const int du = B / R, dk = B - du * R;
+        while (u < U_) {
+            copy(u, k);
+            u += du;
+            k += dk;
+            if (k >= R) {
+                k -= R;
+                ++u;
+            }
+        }
+    };
+    {
+        const cx<T> *hz = H + p0;
+        const cx<T> *v0 = Vtab + col0;
+        walk(U, PIECES, [&](int u, int k) {
+            cp_async16(fbase + (size_t)(2 * u) * B + k * PER16, hz + (size_t)u * ND + k * PER16);
+            if (NYQ) cp_async16(fbase + (size_t)(2 * u + 1) * B + k * PER16, v0 + (size_t)u * VS + k * PER16);
+        });
     }
     if (NYQ && d == 3) {
-        const int RP = N / PER16;
-        for (int i = threadIdx.x; i < U * RP; i += B) {
-            const int u = i / RP, k = (i - u * RP) * PER16;
-            cp_async16(tabs + (size_t)u * TS + k, Vtab + (size_t)u * VS + (size_t)P + (size_t)i1 * N + k);
-        }
-        const int n2 = min(W2, N - i2lo);
-        for (int i = threadIdx.x; i < U * n2; i += B) {
-            const int u = i / n2, k = i - u * n2;
-            cp_async_cx<T>(tabs + (size_t)u * TS + N + k,
-                           Vtab + (size_t)u * VS + (size_t)2 * P + (size_t)i1 * N + i2lo + k);
-        }
+        const cx<T> *v1 = Vtab + (size_t)P + (size_t)i1 * N;
+        walk(U, N / PER16, [&](int u, int k) {
+            cp_async16(tabs + (size_t)u * TS + k * PER16, v1 + (size_t)u * VS + k * PER16);
+        });
+        const cx<T> *v2 = Vtab + (size_t)2 * P + (size_t)i1 * N + i2lo;
+        walk(U, min(W2, N - i2lo), [&](int u, int k) {
+            cp_async_cx<T>(tabs + (size_t)u * TS + N + k, v2 + (size_t)u * VS + k);
+        });
     } else if (NYQ) {
         for (int u = threadIdx.x; u < U; u += B) cp_async_cx<T>(tabs + (size_t)u * TS, Vtab + (size_t)u * VS + N + i1);
     }

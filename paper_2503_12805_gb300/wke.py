@@ -85,7 +85,7 @@ class WkePlanInfo(ctypes.Structure):
 
 EXPORTED = [
     "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
-    "wke_plan_get_info", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
+    "wke_plan_get_info", "wke_plan_describe", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
@@ -378,6 +378,7 @@ class Plan:
         self.d, self.N, self.L = d, N, L
         self.M = n_r * n_s * n_sig
         self.precision = precision
+        self.quad = q                      # the descriptor (its user rules are kept alive above)
         self.handle = wke_plan_create(d, N, L, self.M, q)
 
     @property

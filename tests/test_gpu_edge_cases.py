@@ -127,3 +127,27 @@ def test_lone_group_in_last_chunk():
     scale = np.max(np.abs(ref))
     assert rel_max_err(Q, ref.real, scale) <= 1e-12
     assert rel_max_err(Qim, ref.imag, scale) <= 1e-12
+
+
+DESCRIBE_CASES = [
+    (3, 64, (32, 8, 8), dict(sphere="cube", precision="fp32")),
+    (3, 32, (4, 8, 8), dict(sphere="cube", precision="fp64", layout="per_group")),
+    (3, 32, (4, 8, 8), dict(sphere="cube", precision="split")),
+    (2, 64, (6, 4, 4), dict(sphere="midpoint", precision="fp32", nyquist="zero", dealias=True)),
+    (3, 16, (2, 12, 20), dict(sphere="icosahedron", sphere_sig="dodecahedron", precision="fp64")),
+]
+
+
+@pytest.mark.parametrize("d,N,n,kw", DESCRIBE_CASES)
+def test_describe_matches_created_plan(d, N, n, kw):
+    """wke_plan_describe (host work only) gives the created plan's record; its
+    device bytes, the admission estimate, cover what the plan allocated."""
+    require_cuda()
+    from paper_2503_12805_gb300 import wke
+    with wke.Plan(d, N, L, *n, **kw) as plan:
+        got = plan.info()
+        want = wke.wke_plan_describe(d, N, L, plan.M, plan.quad)
+    for name, _ in wke.WkePlanInfo._fields_:
+        if name != "device_bytes":
+            assert getattr(want, name) == getattr(got, name), name
+    assert got.device_bytes <= want.device_bytes <= got.device_bytes + 4096
