@@ -60,42 +60,34 @@ __device__ __forceinline__ void load_twiddles(cx<T> *tw, const cx<T> *tw_g) {
 }
 
 // ------------------------------------------------------------------ forward
-// 3D: forward transform over axes (1, 2) of every plane i1 of the real input,
-// in double.  One block per plane: row lines along axis 2, then column lines
-// along axis 1 with consecutive columns per warp (coalesced stores).
-template <typename TIn, int N>
-__global__ void __launch_bounds__(N * LineCfg<double, N>::TPL)
-k_fwd_planes_3d(const TIn *__restrict__ f, double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
+// 3D: forward transform along axis 1 of every (i1, i3) line, in place, in
+// double (the rows were transformed by k_fwd_rows_2d over all N^2 rows).  A
+// warp holds LPW lines of consecutive i3.
+template <int N>
+__global__ void k_fwd_mid_3d(double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
     typedef LineCfg<double, N> Cfg;
-    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tw = reinterpret_cast<double2 *>(smem_raw);
-    double2 *work = tw + N;
-    double2 *scratch = work + N * WP;
+    double2 *scratch = tw + N;
     load_twiddles<double, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
-    const int row = warp * LPW + c;
-    const int z = threadIdx.x % N, ty = threadIdx.x / N;
-    double2 *rscr = scratch + (size_t)row * LinePad<N>::PITCH;
-    const int i1 = blockIdx.x;
-    const TIn *src = f + ((size_t)i1 * N + row) * N;
+    const int wl = warp * LPW + c;
+    const int line = blockIdx.x * (blockDim.x / 32) * LPW + wl;
+    const int i1 = line / N, i3 = line - i1 * N;
+    double2 *base = tmp + (size_t)i1 * N * N + i3;
+    double2 *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     double2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = make_double2((double)src[t + e * TPL], 0.0);
-    line_fft<double, N, E, -1>(v, t, rscr, tw);
+    for (int e = 0; e < E; ++e) v[e] = base[(size_t)(t + e * TPL) * N];
+    line_fft<double, N, E, -1>(v, t, scr, tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = work[(ty + e * TPL) * WP + z];
-    col_fft<double, N, E, -1>(v, ty, scratch, z, N, tw);
-    double2 *out = tmp + (size_t)i1 * N * N;
-#pragma unroll
-    for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
+    for (int e = 0; e < E; ++e) base[(size_t)(t + e * TPL) * N] = v[e];
 }
 
-// 2D: forward transform of every row, in double.
+// Forward transform of every row (the last axis), in double: the N rows of a
+// 2D grid, or the N^2 rows of a 3D one.
 template <typename TIn, int N>
 __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
     typedef LineCfg<double, N> Cfg;

@@ -45,9 +45,18 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
-            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(double2);
-            if ((rc = set_smem(k_fwd_planes_3d<T, N>, smem))) return rc;
-            k_fwd_planes_3d<T, N><<<N, N * Cfg::TPL, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
+            // rows (axis 2) of all N^2 rows, then axis 1 of all N^2 lines: line
+            // kernels over the whole grid, so every SM takes part in the FP64 work
+            const int rows = N * N;
+            int warps = 1;                    // at least one block per SM where the grid allows
+            while (2 * warps <= KCfg<double>::WARPS && rows % (2 * warps * Cfg::LPW) == 0 &&
+                   rows / (2 * warps * Cfg::LPW) >= 152)
+                warps *= 2;
+            const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
+            if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
+            k_fwd_rows_2d<T, N><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
+            if ((rc = set_smem(k_fwd_mid_3d<N>, smem))) return rc;
+            k_fwd_mid_3d<N><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
         } else {
             return (int)cudaErrorInvalidValue;
         }
