@@ -33,6 +33,18 @@ template <typename T, int N> static int line_warps(int lines) {
     return std::max(1, std::min(KCfg<T>::WARPS, lines / LineCfg<T, N>::LPW));
 }
 
+// Warps per block of a forward (FP64) line kernel over `lines` lines: the
+// largest power of two up to KCfg::WARPS that keeps at least one block per SM
+// and divides the lines, since FP64 line work is bound by each SM's FP64 units.
+template <int N> static int spread_warps(int lines) {
+    typedef LineCfg<double, N> Cfg;
+    int warps = 1;
+    while (2 * warps <= KCfg<double>::WARPS && lines % (2 * warps * Cfg::LPW) == 0 &&
+           lines / (2 * warps * Cfg::LPW) >= 152)
+        warps *= 2;
+    return warps;
+}
+
 // ------------------------------------------------------------------ forward
 // Forward transform of f on its own grid (N = N_in).  A de-aliased plan
 // writes the coefficients to ghat_in; the padding kernel moves them to the
@@ -48,10 +60,7 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
             // rows (axis 2) of all N^2 rows, then axis 1 of all N^2 lines: line
             // kernels over the whole grid, so every SM takes part in the FP64 work
             const int rows = N * N;
-            int warps = 1;                    // at least one block per SM where the grid allows
-            while (2 * warps <= KCfg<double>::WARPS && rows % (2 * warps * Cfg::LPW) == 0 &&
-                   rows / (2 * warps * Cfg::LPW) >= 152)
-                warps *= 2;
+            const int warps = spread_warps<N>(rows);
             const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
             if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
             k_fwd_rows_2d<T, N><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
@@ -61,12 +70,12 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
             return (int)cudaErrorInvalidValue;
         }
     } else {
-        const int warps = line_warps<double, N>(N);
+        const int warps = spread_warps<N>(N);
         const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
         if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
         k_fwd_rows_2d<T, N><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
     }
-    const int warps = line_warps<double, N>(P);
+    const int warps = spread_warps<N>(P);
     const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
     if ((rc = set_smem(k_fwd_cols<T, N>, smem))) return rc;
     const double inv_nd = 1.0 / (double)nd_in(hp);
