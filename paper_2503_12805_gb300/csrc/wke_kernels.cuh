@@ -218,7 +218,10 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *work = tw + N;
     cx<T> *scratch = work + N * WP;           // row scratch, then column scratch
-    cx<T> *prow = scratch + N * LinePad<N>::PITCH;   // 2 buffers x (field a, field b) x rows 1, 2
+    // 2 buffers of 4N + 2 entries: (field a, field b) x rows 1, 2, then the two
+    // fields' row-0 entries at j1
+    cx<T> *prow = scratch + N * LinePad<N>::PITCH;
+    constexpr int PS = 4 * N + 2;
     load_twiddles<T, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
@@ -229,15 +232,18 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     const int uend = min(nunits, ubeg + units_per_block);
     const size_t NN = (size_t)N * N;
     const int j1 = blockIdx.x;
-    // rows 1 and 2 of unit u's phase tables: prow[buf][0, 2N) field a, [2N, 4N) field b
+    // rows 1 and 2 of unit u's phase tables: prow[buf][0, 2N) field a, [2N, 4N)
+    // field b; [4N], [4N + 1] the row-0 entries at j1 of fields a and b
     auto stage_rows = [&](int u) {
         int fa, fb;
         unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
         const cx<T> *pa = phase + (size_t)fa * 3 * N + N;
         const cx<T> *pb = phase + (size_t)(fb >= 0 ? fb : fa) * 3 * N + N;
-        cx<T> *dst = prow + ((u - ubeg) & 1) * 4 * N;
-        for (int i = threadIdx.x; i < 4 * N; i += blockDim.x)
-            cp_async_cx<T>(dst + i, i < 2 * N ? pa + i : pb + (i - 2 * N));
+        cx<T> *dst = prow + ((u - ubeg) & 1) * PS;
+        for (int i = threadIdx.x; i < PS; i += blockDim.x)
+            cp_async_cx<T>(dst + i, i < 2 * N   ? pa + i
+                                    : i < 4 * N ? pb + (i - 2 * N)
+                                    : (i == 4 * N ? pa : pb) - N + j1);
         cp_async_commit();
     };
     if (ubeg < uend) stage_rows(ubeg);
@@ -252,11 +258,11 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
         else cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();                       // unit u's rows, copied by the whole block
-        const cx<T> *ra = prow + ((u - ubeg) & 1) * 4 * N, *rb = ra + 2 * N;
-        const cx<T> a01 = cmul<T>(phase[(size_t)fa * 3 * N + j1], ra[row]);
+        const cx<T> *ra = prow + ((u - ubeg) & 1) * PS, *rb = ra + 2 * N;
+        const cx<T> a01 = cmul<T>(ra[4 * N], ra[row]);
         cx<T> v[E];
         if (fb >= 0) {
-            const cx<T> b01 = cmul<T>(phase[(size_t)fb * 3 * N + j1], rb[row]);
+            const cx<T> b01 = cmul<T>(ra[4 * N + 1], rb[row]);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j3 = t + e * TPL;

@@ -120,7 +120,7 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t 
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
-            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH + 8 * N) * sizeof(cx<T>);
+            const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH + 8 * N + 4) * sizeof(cx<T>);
             if ((rc = set_smem(k_pass1_3d<T, N>, smem))) return rc;
             // enough blocks to fill the GPU several times over
             // automatic: 2 units per block in the shared-field layout (13-unit chunks
