@@ -58,6 +58,18 @@ __device__ __forceinline__ void load_twiddles(cx<T> *tw, const cx<T> *tw_g) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
     __syncthreads();
 }
+// The same in two steps: the global load issued first, so that it is in
+// flight together with a kernel's own first loads, and the shared-memory
+// store and barrier once those are issued.
+template <typename T, int N> __device__ __forceinline__ cx<T> twiddle_fetch(const cx<T> *tw_g) {
+    return threadIdx.x < N ? tw_g[threadIdx.x] : mkc<T>((T)0, (T)0);
+}
+template <typename T, int N>
+__device__ __forceinline__ void twiddle_store(cx<T> *tw, cx<T> mine, const cx<T> *tw_g) {
+    if (threadIdx.x < N) tw[threadIdx.x] = mine;
+    for (int i = threadIdx.x + blockDim.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    __syncthreads();
+}
 
 // ------------------------------------------------------------------ forward
 // 3D: forward transform along axis 1 of every (i1, i3) line, in place, in
@@ -222,7 +234,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     // fields' row-0 entries at j1
     cx<T> *prow = scratch + N * LinePad<N>::PITCH;
     constexpr int PS = 4 * N + 2;
-    load_twiddles<T, N>(tw, tw_g);
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int row = warp * LPW + c;           // axis-1 index j2 of this row line
@@ -251,6 +263,7 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     cx<T> g[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) g[e] = grow[t + e * TPL];
+    twiddle_store<T, N>(tw, twv, tw_g);
     for (int u = ubeg; u < uend; ++u) {
         int fa, fb;
         unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
@@ -361,7 +374,7 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *work = tw + N;
     cx<T> *scratch = work + N * WP;
-    load_twiddles<T, N>(tw, tw_g);
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int row = warp * LPW + c;           // index along b0
@@ -395,6 +408,7 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
             hb = herm_half<T>(cmul<T>(s0, cmul<T>(rb, pb[b1 * N + col])), cmul<T>(s1, cmul<T>(rmb, pb[b1 * N + mcol])));
         v[e] = mkc<T>(ha.x - hb.y, ha.y + hb.x);
     }
+    twiddle_store<T, N>(tw, twv, tw_g);
     line_fft<T, N, E, +1>(v, t, rscr, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = v[e];
@@ -656,13 +670,14 @@ k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
-    load_twiddles<T, N>(tw, tw_g);
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
     const int z = threadIdx.x % CB, t = threadIdx.x / CB;
     const int col = blockIdx.x * CB + z;
     cx<T> *Hu = H + (size_t)blockIdx.y * N * P + col;
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = Hu[(size_t)(t + e * TPL) * P];
+    twiddle_store<T, N>(tw, twv, tw_g);
     col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) Hu[(size_t)(t + e * TPL) * P] = v[e];
