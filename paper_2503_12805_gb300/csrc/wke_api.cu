@@ -526,7 +526,9 @@ static void fill_info(const HostPlan &hp, wke_plan_info *info) {
     info->products_per_group = hp.products_per_group;
     info->groups_per_chunk = hp.groups_per_chunk;
     info->n_chunks = hp.n_chunks;
-    info->launches_per_collision = 2 + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1 +
+    // forward: one line kernel per axis; per chunk pass 1, (Nyquist tables), pass 2 or
+    // axis 0 + products; finalize
+    info->launches_per_collision = hp.d + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1 +
                                    (hp.shared ? hp.n_chunks : 0) +
                                    (hp.dealias ? 1 + 2 * hp.d : 0);
     info->flops_per_collision = plan_flops(hp);

@@ -141,7 +141,7 @@ def test_shared_field_layout_counts(wke):
     info = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32)
     assert info.shared_fields == 1 and info.products_per_group == 3
     assert info.n_chunks == 32 and info.units_per_collision == 32 * 13
-    assert info.launches_per_collision == 2 + 4 * 32 + 1
+    assert info.launches_per_collision == 3 + 4 * 32 + 1     # forward: rows, axis 1, axis 0
     fp64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP64)
     assert fp64.units_per_collision == 32 * 13            # a whole radius fits the FP64 budget
     per_group = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, layout=wke.WKE_LAYOUT_PER_GROUP)
@@ -161,3 +161,61 @@ def test_describe_matches_footprint_and_rejects_like_create(wke):
     assert info.device_bytes == wke.wke_plan_footprint_bytes(3, 32, 8.0, 256, q)
     info2 = wke.WkePlanInfo()
     assert wke.lib().wke_plan_describe(3, 128, 8.0, 256, ctypes.byref(q), ctypes.byref(info2)) == -4
+
+
+LAYOUT_CASES = [
+    # d, N, (n_r, n_s, n_sig), q-hat rule, sigma rule, precision, Nyquist modes
+    (2, 128, (32, 4, 4), "midpoint", None, "fp32", "keep"),
+    (2, 64, (6, 6, 6), "midpoint", None, "fp32", "zero"),
+    (2, 32, (5, 5, 3), "midpoint", None, "fp64", "keep"),
+    (3, 64, (32, 8, 8), "cube", None, "fp32", "keep"),
+    (3, 32, (16, 8, 8), "cube", None, "fp64", "keep"),
+    (3, 32, (2, 12, 20), "icosahedron", "dodecahedron", "fp32", "keep"),
+    (3, 48, (6, 8, 8), "cube", None, "fp32", "zero"),
+    (3, 16, (3, 8, 6), "cube", "product:2:3", "fp64", "keep"),
+]
+
+
+@pytest.mark.parametrize("d,N,n,sph,sph_sig,prec,nyq", LAYOUT_CASES)
+def test_layout_invariants(wke, d, N, n, sph, sph_sig, prec, nyq):
+    """Plan records from wke_plan_describe (host work only): shapes, the launch
+    count of each layout, and the automatic choice of the shared-field layout
+    exactly when it transforms at most 85% of the per-group layout's units."""
+    M = n[0] * n[1] * n[2]
+
+    def describe(layout):
+        q = wke.wke_quadrature_default()
+        q.n_r, q.n_s, q.n_sig = n
+        q.sphere_rule, q.sphere_param = wke._rule(sph)
+        if sph_sig is not None:
+            q.sphere_rule_sig, q.sphere_param_sig = wke._rule(sph_sig)
+        q.precision = {"fp64": wke.WKE_FP64, "fp32": wke.WKE_FP32}[prec]
+        q.nyquist = {"keep": wke.WKE_NYQ_KEEP, "zero": wke.WKE_NYQ_ZERO}[nyq]
+        q.layout = layout
+        info = wke.WkePlanInfo()
+        rc = wke.lib().wke_plan_describe(d, N, 8.0, M, ctypes.byref(q), ctypes.byref(info))
+        return rc, info
+
+    rc, per_group = describe(wke.WKE_LAYOUT_PER_GROUP)
+    assert rc == 0
+    rc, auto = describe(wke.WKE_LAYOUT_AUTO)
+    assert rc == 0
+    rc_shared, shared = describe(wke.WKE_LAYOUT_SHARED)
+    for info in (per_group, auto) + ((shared,) if rc_shared == 0 else ()):
+        assert (info.d, info.N, info.M) == (d, N, M)
+        assert info.n_groups == n[0] * n[1]
+        assert info.n_chunks >= 1 and info.units_per_collision >= 1 and info.device_bytes > 0
+        # forward (one kernel per axis), per chunk pass 1 (+ Nyquist tables) and
+        # pass 2, or axis 0 + products in the shared layout, then finalize
+        per_chunk = (3 if nyq == "keep" else 2) + info.shared_fields
+        assert info.launches_per_collision == d + per_chunk * info.n_chunks + 1
+    assert per_group.shared_fields == 0
+    if rc_shared == 0:
+        assert shared.shared_fields == 1
+        pick = shared.units_per_collision <= 0.85 * per_group.units_per_collision
+        assert auto.shared_fields == int(pick)
+        chosen = shared if pick else per_group
+        assert auto.units_per_collision == chosen.units_per_collision
+        assert auto.n_chunks == chosen.n_chunks
+    else:
+        assert auto.shared_fields == 0
