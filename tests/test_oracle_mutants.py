@@ -82,6 +82,42 @@ MUTANTS = [
      "    return iFFT(fhat * phase(d, N, L, x), L)",
      "    return iFFT(fhat * np.swapaxes(phase(d, N, L, x), 0, 1), L)",
      pins.fast_vs_realspace, 2),
+    ("point evaluator: phase of the shift with the wrong sign",
+     "np.exp(1j * math.pi / L * np.outer(kpt[ax] - Xc[:, ax], j1))",
+     "np.exp(1j * math.pi / L * np.outer(kpt[ax] + Xc[:, ax], j1))",
+     pins.at_points_vs_fast, 3),
+    ("point evaluator: first axis's phases on the last axis",
+     "t = fhat.reshape(-1, N) @ e[d - 1].T", "t = fhat.reshape(-1, N) @ e[0].T",
+     pins.at_points_vs_fast, 2),
+    ("point evaluator: contraction over the axes in the wrong order",
+     "for ax in range(d - 2, -1, -1):", "for ax in range(d - 1):",
+     pins.at_points_vs_fast, 3),
+    ("moments: cell volume h^(d-1)",
+     "    w = h ** d\n", "    w = h ** (d - 1)\n",
+     pins.moments_gaussian, 3),
+    ("moments: grid without its -L offset in the momentum",
+     "out += [w * np.sum(g * k[..., a]) for a in range(d)]",
+     "out += [w * np.sum(g * (k[..., a] + L)) for a in range(d)]",
+     pins.moments_gaussian, 2),
+    ("moments: energy weight (sum k)^2 instead of |k|^2",
+     "out += [w * np.sum(g * np.sum(k * k, axis=-1))]",
+     "out += [w * np.sum(g * np.sum(k, axis=-1) ** 2)]",
+     pins.moments_gaussian, 2),
+]
+
+# Mistakes in the time integrator: the pin is the observed order of accuracy,
+# which a correct oracle meets to about 0.2 and a wrong stage weight or stage
+# argument misses by at least one order.
+RK_MUTANTS = [
+    ("RK4: weights 1/3 instead of 1/6, 1/3, 1/3, 1/6",
+     "return f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)",
+     "return f + dt / 3.0 * (k1 + k2 + k3 + k4)", 2),
+    ("RK4: third stage from k1 instead of k2",
+     "k3 = Q(f + 0.5 * dt * k2)", "k3 = Q(f + 0.5 * dt * k1)", 3),
+    ("RK4: fourth stage at half the step",
+     "k4 = Q(f + dt * k3)", "k4 = Q(f + 0.5 * dt * k3)", 2),
+    ("Heun: second stage at half the step",
+     "k2 = Q(f + dt * k1)", "k2 = Q(f + 0.5 * dt * k1)", 2),
 ]
 
 
@@ -102,6 +138,12 @@ def _mutant(old, new):
 def test_pin_catches_planted_mistake(name, old, new, pin, d):
     err = pin(_mutant(old, new), d)
     assert err > 1e-6, f"pin {pin.__name__} did not see: {name} (discrepancy {err:.3g})"
+
+
+@pytest.mark.parametrize("name,old,new,d", RK_MUTANTS, ids=[m[0] for m in RK_MUTANTS])
+def test_rk_order_pin_catches_planted_mistake(name, old, new, d):
+    defect = pins.rk_order_defect(_mutant(old, new), d)
+    assert defect > 0.6, f"order pin did not see: {name} (order defect {defect:.3g})"
 
 
 def test_unmutated_copy_passes():

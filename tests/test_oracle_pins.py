@@ -270,3 +270,28 @@ def test_rj_residual_trend_matches_paper_table():
     assert all(ours[Ns[i + 1]] < ours[Ns[i]] for i in range(len(Ns) - 1)), ours
     paper64 = [v for N, ns, v in rows if N == 64][0]
     assert 0.1 < ours[64] / paper64 < 10.0, (ours[64], paper64)
+
+
+# ------------------------------------------------------------ evaluators used as GPU references
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_collision_at_points_matches_fast_form(d):
+    """The point evaluator (the reference of the full-size sampled GPU
+    checks) equals the FFT route at random grid points to rounding."""
+    assert pins.at_points_vs_fast(O, d) < 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_moments_match_gaussian_closed_forms(d):
+    """Mass, momentum and energy of a shifted Gaussian (Sec. 2 definitions)."""
+    assert pins.moments_gaussian(O, d) < 1e-11
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rk_step_orders_of_accuracy(d):
+    """Euler, Heun and classical RK4 converge at orders 1, 2 and 4 against an
+    independent ODE solution: a wrong stage weight or stage argument lowers
+    the observed order."""
+    orders = pins.rk_orders(O, d)
+    for p in (1, 2, 4):
+        assert abs(orders[p] - p) < 0.3, orders
