@@ -33,9 +33,6 @@ import wke_inputs as I  # noqa: E402
 METRIC = "Q(f) evals/s at 3D N=64 (FP32/split vs FP64 GPU, ≤1e-6 rel); serving p50/p99 ms"
 UNIT = "evals/s"
 WORKLOAD = I.WORKLOADS["3d_n64_m2048"]
-PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 
 
 def _config(precision="fp32"):
@@ -106,15 +103,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def _oracle_chunk(args):
-    lo, hi = args
-    import numpy as np  # noqa: F401
+def _oracle_quad_args():
     from oracle import wke_oracle as O
     w = WORKLOAD
-    quad = O.make_quadrature(w.d, w.n_r, w.n_s, w.n_sig, O.default_R(w.L), w.sphere)
-    t = time.perf_counter()
-    O.collision_fast(w.initial(), w.L, quad, node_range=(lo, hi))
-    return time.perf_counter() - t
+    return (w.d, w.n_r, w.n_s, w.n_sig, O.default_R(w.L), w.sphere)
+
+
+def cpu_oracle_rate(pool, evals):
+    """Evaluations/s of the FP64 oracle's fast form on the host cores: `evals`
+    whole evaluations of the workload, each split over node ranges across the
+    spawn pool's processes (oracle.pool) and summed in node order."""
+    w = WORKLOAD
+    f = w.initial()
+    walls = []
+    for _ in range(evals):
+        _, wall, _ = pool.collision_fast(f, w.L, _oracle_quad_args())
+        walls.append(wall)
+    return evals / sum(walls), walls
 
 
 def replica_rate(t_step_ms, world, device=None):
@@ -131,36 +136,13 @@ def replica_rate(t_step_ms, world, device=None):
     return t_max, world * 1000.0 / t_max
 
 
-def cpu_oracle_rate(pool, nodes_per_worker, workers):
-    """Evaluations/s of the FP64 oracle on `workers` host processes, from a
-    bounded sample: each worker sums `nodes_per_worker` nodes of the workload."""
-    w = WORKLOAD
-    group = w.n_sig
-    ranges = []
-    for k in range(workers):
-        lo = (k * nodes_per_worker // group) * group % w.M
-        ranges.append((lo, min(w.M, lo + nodes_per_worker)))
-    t = time.perf_counter()
-    list(pool.map(_oracle_chunk, ranges))
-    wall = time.perf_counter() - t
-    nodes = sum(h - l for l, h in ranges)
-    return (nodes / w.M) / wall, wall, nodes
-
-
 def make_pool():
-    import multiprocessing as mp
-    workers = os.cpu_count() or 1
-    return mp.get_context("spawn").Pool(workers), workers
+    from oracle.pool import OraclePool
+    pool = OraclePool()
+    return pool, pool.workers
 
 
 # ------------------------------------------------------------------ GPU arm
-
-def _measured_peaks():
-    try:
-        return json.load(open(PEAKS_PATH))
-    except (OSError, ValueError):
-        return {}
-
 
 def run_gpu(args, rank, world, pool, workers):
     import numpy as np
@@ -204,6 +186,13 @@ def run_gpu(args, rank, world, pool, workers):
         if world > 1:
             torch.distributed.barrier()
         return ms, wall, prof
+
+    # measured FP32 and FP64 FMA rates of this GPU (the ALU roofs)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    with ClockSampler(dev.index) as pclk:
+        peaks32 = wke.wke_alu_peak(wke.WKE_FP32, 5)
+        peaks64 = wke.wke_alu_peak(wke.WKE_FP64, 3)
+    peak_clocks = pclk.summary()
 
     # FP32 headline (no per-kernel events in this loop); the launch layout is
     # picked by the library's autotuner before the timed region
@@ -259,32 +248,16 @@ def run_gpu(args, rank, world, pool, workers):
         p32.collision_host(fh, qh)
     e2e_rate = world * e2e_steps / (time.perf_counter() - t0)
 
-    # roofline of the dominant kernel class
-    peaks = _measured_peaks()
-    classes = {c: v for c, v in prof.items() if v[1] > 0}
-    dom = max(classes, key=lambda c: classes[c][0])
-    dom_ms, dom_n = classes[dom]
-    per_launch_ms = dom_ms / dom_n
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    share = {c: round(v[0] / sum(x[0] for x in classes.values()), 4) for c, v in classes.items()}
-    if info.shared_fields and dom == "pass2":
-        # the product pass streams the chunk's transformed units: bytes against the copy bandwidth
-        hbm = peaks.get("hbm_gbs")
-        achieved = kernel_bytes(dom, info) / (per_launch_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "products", "achieved": round(achieved, 1),
-                    "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if hbm else None,
-                    "traffic": PRODUCTS_DRAM_BYTES_3D_N64 if (info.d, info.N_compute) == (3, 64) else None,
-                    "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)" if hbm else "absent",
-                    "algorithmic_bytes_per_launch": round(kernel_bytes(dom, info)),
-                    "alu_frac": round(kernel_flops(dom, info) / (per_launch_ms * 1e-3) / 1e12 / alu_peak, 4)}
-    else:
-        achieved = kernel_flops(dom, info) / (per_launch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
-                    "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
-                    "traffic": None,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
-    roofline.update({"per_launch_ms": round(per_launch_ms, 5), "launches": dom_n, "kernel_share": share})
+    # roofline of the dominant kernel class: every kernel works on chunk units
+    # resident in L2 (DRAM traffic per launch is kilobytes), so the binding
+    # roof is the FP32 ALU rate, measured here by the library's FMA probe
+    roofline = roofline_of(prof, info, peaks32)
+    fp64_info = p64.info()
+    fp64_alu = {"evals_per_s": round(fp64_rate, 4), "executed_flops_per_eval": fp64_info.flops_per_collision,
+                "achieved_tflops": round(fp64_info.flops_per_collision * fp64_rate / 1e12, 4),
+                "peak_tflops": round(peaks64[0], 4),
+                "frac": round(fp64_info.flops_per_collision * fp64_rate / 1e12 / peaks64[0], 4),
+                "peak_source": "wke_alu_peak(WKE_FP64): DFMA chains on every SM, measured in this run"}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -296,7 +269,9 @@ def run_gpu(args, rank, world, pool, workers):
         "e2e": {"value": round(e2e_rate, 3), "unit": UNIT, "h2d_bytes_per_step": fh.numel() * 4,
                 "d2h_bytes_per_step": qh.numel() * 4},
         "gpu_launches": args.steps * info.launches_per_collision,
-        "clocks": clocks, "roofline": roofline,
+        "clocks": clocks, "roofline": roofline, "fp64_roofline": fp64_alu,
+        "alu_peaks_measured": {"fp32_tflops": round(peaks32[0], 3), "fp64_tflops": round(peaks64[0], 4),
+                               "sms": sms, "clocks": peak_clocks},
         "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
                    "pass1_units_per_block": tuning.pass1_units_per_block, "autotune_ms": round(tune_ms, 4)},
         "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
@@ -310,11 +285,11 @@ def run_gpu(args, rank, world, pool, workers):
     if args.serve_requests > 0:
         line["serving"] = run_serving(args.serve_requests, I.BASE_SEED + 4 + rank, wke, 40 << 30, 8)
     if rank == 0 and pool is not None:
-        rate, wall, nodes = cpu_oracle_rate(pool, args.oracle_nodes, workers)
+        rate, walls = cpu_oracle_rate(pool, args.oracle_evals)
         line["cpu_baseline"] = {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
-                                "sample": f"{nodes} of {w.M} nodes of one evaluation ({args.oracle_nodes} per "
-                                          f"process, {workers} spawn processes, {wall:.1f} s wall), scaled to "
-                                          "full evaluations"}
+                                "sample": f"{len(walls)} whole evaluations of the workload (FP64 fast form, "
+                                          f"node ranges over {workers} spawn processes, partial sums added "
+                                          f"in node order), {sum(walls):.1f} s wall"}
     p32.close()
     p64.close()
     return line
@@ -355,21 +330,61 @@ def kernel_flops(cls, info):
     return 2.0 * groups * nd
 
 
-# DRAM bytes (read + write) of one product-pass launch at 3D N=64, M=2048,
-# FP32, warm L2, from an ncu capture of this kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum); reported as the roofline's measured traffic for
-# that workload only.
-PRODUCTS_DRAM_BYTES_3D_N64 = 4608 + 37120
-
-
-def kernel_bytes(cls, info, cxb=8, tb=4):
-    """Algorithmic bytes of one launch of the product pass (shared-field
-    layout): every unit of the chunk read once (complex), its d Nyquist
-    tables read once, f read, the FP64 accumulator read and written."""
+def survey_flops(cls, info):
+    """Flops of one launch of a kernel class by the per-node count of the
+    paper's algorithm (Sec. 3.4 complexity paragraph): per node 2 + 1/N_sig
+    inverse transforms of N^d points at 5 N^d log2 N^d flops, 6 d N^d for the
+    phase products and 32 N^d for the cubic products, and one forward
+    transform per evaluation.  The transform's axes split between pass 1
+    (the d - 1 trailing axes) and the axis-0 kernel.  The executed algorithm
+    does less: it transforms each distinct shifted field once and evaluates
+    each distinct product once."""
     d, N = info.d, info.N_compute
-    nd = N ** d
-    units = info.units_per_collision / info.n_chunks
-    return units * nd * cxb + units * d * (nd // N) * cxb + nd * tb + 2 * nd * 8
+    nd = float(N) ** d
+    n_sig = info.M / info.n_groups
+    nodes = info.M / info.n_chunks
+    fields = nodes * (2.0 + 1.0 / n_sig)
+    if cls == "forward":
+        return 5.0 * nd * math.log2(nd)
+    if cls == "pass1":
+        return fields * (5.0 * nd * math.log2(nd / N) + 6.0 * d * nd)
+    if cls == "axis0":
+        return fields * 5.0 * nd * math.log2(N)
+    if cls == "pass2":
+        prod = 32.0 * nodes * nd
+        return prod if info.shared_fields else prod + fields * 5.0 * nd * math.log2(N)
+    return 0.0
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
+# kernel class, from an ncu capture of the current kernels at 3D N=64,
+# M=2048, FP32 (warm L2); None when the kernel changed after the capture.
+DRAM_BYTES_3D_N64 = {}
+
+
+def roofline_of(prof, info, peak32):
+    """Roofline object of the dominant kernel class (largest share of the
+    serialised per-kernel CUDA-event time): executed flops per launch over the
+    measured per-launch time against the measured FP32 FMA rate."""
+    classes = {c: v for c, v in prof.items() if v[1] > 0}
+    total = sum(v[0] for v in classes.values())
+    dom = max(classes, key=lambda c: classes[c][0])
+    dom_ms, dom_n = classes[dom]
+    per_launch_s = dom_ms / dom_n * 1e-3
+    peak = peak32[0]
+    achieved = kernel_flops(dom, info) / per_launch_s / 1e12
+    paper = survey_flops(dom, info) / per_launch_s / 1e12
+    traffic = DRAM_BYTES_3D_N64.get(dom) if (info.d, info.N_compute, info.precision) == (3, 64, 1) else None
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": "wke_alu_peak(WKE_FP32): FMA chains on every SM, measured in this run (of measured)",
+            "flops_per_launch": kernel_flops(dom, info),
+            "paper_algorithm_flops_per_launch": survey_flops(dom, info),
+            "paper_algorithm_achieved": round(paper, 3), "paper_algorithm_frac": round(paper / peak, 4),
+            "per_launch_ms": round(dom_ms / dom_n, 5), "launches": dom_n,
+            "kernel_share": {c: round(v[0] / total, 4) for c, v in classes.items()},
+            "class_frac": {c: round(kernel_flops(c, info) / (v[0] / v[1] * 1e-3) / 1e12 / peak, 4)
+                           for c, v in classes.items()}}
 
 
 # ------------------------------------------------------------------ de-aliased variant
@@ -514,30 +529,37 @@ def run_serving(n_requests, seed, wke, budget_bytes, max_active):
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU FP64 oracle (the only other program that
+    computes this operator), one whole evaluation of the workload per step
+    over the host cores.  The warm-up steps evaluate the nodes of one radius
+    each (they start the worker processes and their imports)."""
     if rank != 0:
         return None
+    from oracle import wke_oracle as O
     pool, workers = make_pool()
-    # per-step sample sized so that the whole run stays near two minutes:
-    # one oracle node costs about 0.06 s per process on the GPU machine's host
-    per_step = max(1, min(args.oracle_nodes, int(120.0 / (max(1, args.steps) * 0.06))))
+    w = WORKLOAD
+    f = w.initial()
+    qa = _oracle_quad_args()
     try:
-        rates = []
+        for _ in range(args.warmup):
+            pool.collision_fast(f, w.L, (qa[0], 1) + qa[2:])
+        walls = []
         t0 = time.perf_counter()
-        for _ in range(min(args.warmup, 3)):
-            cpu_oracle_rate(pool, max(1, per_step // 2), workers)
         for _ in range(args.steps):
-            rates.append(cpu_oracle_rate(pool, per_step, workers)[0])
+            walls.append(pool.collision_fast(f, w.L, qa)[1])
         wall = time.perf_counter() - t0
     finally:
         pool.close()
-    rate = statistics.median(rates)
+    del O
+    ms = 1000.0 * sum(walls) / len(walls)
+    rate = 1000.0 / ms
     return {"impl": "reference", "metric": METRIC, "value": round(rate, 6), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / rate, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config("fp64 (CPU oracle)"),
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
-                             "sample": f"{per_step} nodes per process per step, {workers} spawn "
-                                       f"processes, scaled to full evaluations; {wall:.1f} s wall"},
+                             "sample": f"{args.steps} whole evaluations, one per step, node ranges over "
+                                       f"{workers} spawn processes; {wall:.1f} s wall"},
             "e2e": {"value": round(rate, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -547,8 +569,8 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--oracle-nodes", type=int, default=16,
-                    help="oracle nodes per host process per sample")
+    ap.add_argument("--oracle-evals", type=int, default=2,
+                    help="whole oracle evaluations timed for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch layout")
     ap.add_argument("--no-rk", dest="rk", action="store_false", help="skip the time-stepping section")

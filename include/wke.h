@@ -306,6 +306,19 @@ int wke_plan_profile_read(wke_plan *plan, double *out_host);
 int wke_moments_noalloc(int d, int N, double L, int precision, const void *g_dev, double *out_dev,
                         void *stream);
 
+/* Arithmetic roofs of the current device (a measurement service of the
+ * library; the paper has no counterpart).  Launches register-resident chains
+ * of fused multiply-adds on every SM (4 blocks of 256 threads per SM, 8
+ * independent chains per thread), times `reps` launches after one warm-up
+ * with CUDA events on a private stream, and returns the best rate in
+ * *tflops (2 flops per multiply-add).  precision WKE_FP32 times both the
+ * scalar FMA and the packed two-lane f32x2 FMA and keeps the faster;
+ * WKE_FP64 times the double FMA.  *best_ms (may be NULL) receives the
+ * duration of the best launch.  Allocates and frees a small scratch buffer;
+ * synchronises.  Errors: WKE_ERR_INVALID (precision, reps outside
+ * [1, 1000], tflops NULL), WKE_ERR_OOM, WKE_ERR_CUDA. */
+int wke_alu_peak(int precision, int reps, double *tflops, double *best_ms);
+
 /* ------------------------------------------------------------ serving */
 /* A serving loop runs time-stepping requests of mixed sizes from concurrent
  * simulations with continuous batching: a worker thread admits the oldest

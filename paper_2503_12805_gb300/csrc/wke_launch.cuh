@@ -20,6 +20,26 @@ template <typename K> static int set_smem(K kernel, size_t bytes) {
     return (int)e;
 }
 
+// Streaming multiprocessors of the current device (queried once per device;
+// grids of the grid-stride kernels are sized in multiples of it).
+static inline int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 static inline size_t nd_of(const HostPlan &hp) { return hp.d == 2 ? (size_t)hp.N * hp.N : (size_t)hp.N * hp.N * hp.N; }
 // points of f and Q (the N_in grid; the transform grid N is twice as fine
 // in a de-aliased plan)
@@ -40,7 +60,7 @@ template <int N> static int spread_warps(int lines) {
     typedef LineCfg<double, N> Cfg;
     int warps = 1;
     while (2 * warps <= KCfg<double>::WARPS && lines % (2 * warps * Cfg::LPW) == 0 &&
-           lines / (2 * warps * Cfg::LPW) >= 152)
+           lines / (2 * warps * Cfg::LPW) >= num_sms())
         warps *= 2;
     return warps;
 }
@@ -232,7 +252,7 @@ static int products_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStr
                         (size_t)cr.ng * hp.products_per_group * sizeof(ProdEntry<T>) + (size_t)cr.ng * sizeof(int);
     int rc = 0;
     if ((rc = set_smem(k_products<T, IM, NYQ, PPGC>, smem))) return rc;
-    const int blocks = (int)std::min<size_t>((ND + kProductThreads - 1) / kProductThreads, 152 * 16);
+    const int blocks = (int)std::min<size_t>((ND + kProductThreads - 1) / kProductThreads, num_sms() * 16);
     k_products<T, IM, NYQ, PPGC><<<blocks, kProductThreads, smem, s>>>(
         static_cast<const cx<T> *>(p.H), static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc,
         p.Qacc_im, p.group_cfield, p.prod_local, p.prod_W, hp.d, hp.N, P, cr.g0, cr.ng, cr.sK,
@@ -388,7 +408,7 @@ template <typename T>
 int finalize_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cudaStream_t s) {
     const size_t ND = nd_of(hp);
     const int threads = 256;
-    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
+    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, num_sms() * 8);
     k_finalize<T><<<blocks, threads, 0, s>>>(p.Qacc, Qim ? p.Qacc_im : nullptr, n_accumulators(hp), ND, hp.scale,
                                              static_cast<T *>(Q), static_cast<T *>(Qim));
     return (int)cudaGetLastError();
@@ -407,7 +427,7 @@ template <typename T>
 int rk_stage_T(const HostPlan &hp, const void *f, const void *k, double *kacc, void *ystage, double b_s,
                double c_next_dt, int first, cudaStream_t s) {
     const size_t ND = nd_in(hp);
-    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, num_sms() * 8);
     k_rk_stage<T><<<blocks, 256, 0, s>>>(static_cast<const T *>(f), static_cast<const T *>(k), kacc,
                                           static_cast<T *>(ystage), b_s, c_next_dt, first, ND);
     return (int)cudaGetLastError();
@@ -415,7 +435,7 @@ int rk_stage_T(const HostPlan &hp, const void *f, const void *k, double *kacc, v
 
 template <typename T> int rk_final_T(const HostPlan &hp, void *f, const double *kacc, double dt, cudaStream_t s) {
     const size_t ND = nd_in(hp);
-    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, num_sms() * 8);
     k_rk_final<T><<<blocks, 256, 0, s>>>(static_cast<T *>(f), kacc, dt, ND);
     return (int)cudaGetLastError();
 }
@@ -426,7 +446,7 @@ template <typename TIn, typename TOut>
 static int axis_map(const TIn *in, TOut *out, TOut *out_im, const double2 *K, int n_out, int n_in, size_t A, size_t B,
                     cudaStream_t s) {
     const size_t total = A * (size_t)n_out * B;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, num_sms() * 16);
     k_axis_map<TIn, TOut><<<blocks, 256, 0, s>>>(in, out, out_im, K, n_out, n_in, A, B);
     return (int)cudaGetLastError();
 }
@@ -435,7 +455,7 @@ static int axis_map(const TIn *in, TOut *out, TOut *out_im, const double2 *K, in
 // F = f_N on the 2N grid, by the per-axis interpolation map applied to f.
 template <typename T> int dealias_prepare_T(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
     const size_t ND = nd_of(hp);
-    const int blocks = (int)std::min<size_t>((ND + 255) / 256, 152 * 8);
+    const int blocks = (int)std::min<size_t>((ND + 255) / 256, num_sms() * 8);
     k_pad_spectrum<T><<<blocks, 256, 0, s>>>(static_cast<const cx<T> *>(p.ghat_in), static_cast<cx<T> *>(p.ghat), hp.d,
                                              hp.N_in, hp.N, ND);
     int rc = (int)cudaGetLastError();
@@ -462,7 +482,7 @@ template <typename T> int dealias_prepare_T(const HostPlan &hp, const DevicePtrs
 template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cudaStream_t s) {
     const size_t ND = nd_of(hp);
     const int threads = 256;
-    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, 152 * 8);
+    const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, num_sms() * 8);
     double *qf = static_cast<double *>(p.map0);
     k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, n_accumulators(hp), ND, hp.scale, qf, nullptr);
     int rc = (int)cudaGetLastError();

@@ -89,7 +89,8 @@ EXPORTED = [
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
-    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_last_error_string", "wke_version",
+    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_alu_peak", "wke_last_error_string",
+    "wke_version",
 ]
 PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist", "axis0")
 
@@ -126,6 +127,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_plan_use_graphs": (i, [vp, i]),
         "wke_plan_profile": (i, [vp, i]),
         "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
+        "wke_alu_peak": (i, [i, i, C_DOUBLE_P, C_DOUBLE_P]),
         "wke_last_error_string": (ctypes.c_char_p, []),
         "wke_version": (ctypes.c_char_p, []),
     }
@@ -257,6 +259,13 @@ def wke_plan_profile_read(plan) -> dict:
     out = (ctypes.c_double * (2 * len(PROF_CLASSES)))()
     _check(lib().wke_plan_profile_read(plan, out))
     return {c: (out[2 * i], int(out[2 * i + 1])) for i, c in enumerate(PROF_CLASSES)}
+
+
+def wke_alu_peak(precision: int, reps: int = 5):
+    """Measured FMA throughput of the current device: (TFLOP/s, ms of the best launch)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().wke_alu_peak(precision, reps, ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def wke_server_create(device_budget_bytes: int, max_active: int):

@@ -131,6 +131,40 @@ def test_workload_3d_n64_m2048_sampled(prec):
     assert rel_max_err(goti, ref.imag, scale) <= TOL[prec]
 
 
+@pytest.fixture(scope="module")
+def headline_reference():
+    """The oracle's fast form of the 3D N=64, M=2048 workload over the whole
+    grid, evaluated over node ranges on every host core (spawn pool) and
+    summed in node order."""
+    from oracle.pool import OraclePool
+    w = I.WORKLOADS["3d_n64_m2048"]
+    f = w.initial()
+    with OraclePool() as pool:
+        ref, wall, _ = pool.collision_fast(f, w.L, (3, w.n_r, w.n_s, w.n_sig, O.default_R(w.L), w.sphere))
+    return f, ref
+
+
+# The headline workload is held to the north-star figures over the whole grid:
+# FP64 1e-12, and 1e-6 for both the FP32 path and the split-precision path.
+HEADLINE_TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-6}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "split"])
+def test_workload_3d_n64_m2048_full_field(headline_reference, prec):
+    """3D N=64, M=2048 (32 radial x 8 x 8 cube, ring f), in the configuration
+    the benchmark times, against the oracle at every grid point: Re Q and
+    Im Q, relative max-norm against max |Q|."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["3d_n64_m2048"]
+    f, ref = headline_reference
+    with _plan(wke, 3, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+        Q, Qim = gpu_collision(torch, plan, f, want_imag=True)
+    scale = np.max(np.abs(ref))
+    assert rel_max_err(Q, ref.real, scale) <= HEADLINE_TOL[prec]
+    assert rel_max_err(Qim, ref.imag, scale) <= HEADLINE_TOL[prec]
+
+
 def test_3d_n64_full_field_small_quadrature():
     """N = 64 in 3D over the whole grid (fewer nodes so the oracle stays fast)."""
     torch = require_cuda()

@@ -295,3 +295,17 @@ def test_rk_step_orders_of_accuracy(d):
     orders = pins.rk_orders(O, d)
     for p in (1, 2, 4):
         assert abs(orders[p] - p) < 0.3, orders
+
+
+def test_pooled_fast_form_equals_single_call():
+    """The process-parallel driver (node ranges of whole groups, partial sums
+    added in node order) gives the single-call fast form to rounding."""
+    from oracle.pool import OraclePool, node_ranges
+    assert node_ranges(2048, 8, 16)[0] == (0, 128) and node_ranges(2048, 8, 16)[-1][1] == 2048
+    assert node_ranges(12, 4, 5) == [(0, 4), (4, 8), (8, 12)]
+    quad_args = (3, 3, 8, 6, O.default_R(L), "cube", "octahedron")
+    f = I.gaussian_noise(3, 8, L, 3, eps=0.2)
+    ref = O.collision_fast(f, L, O.make_quadrature(*quad_args), return_complex=True)
+    with OraclePool(2) as pool:
+        got, _, _ = pool.collision_fast(f, L, quad_args, parts=5)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
