@@ -25,6 +25,8 @@ template <typename T> int rk_final_T(const HostPlan &, void *, const double *, d
 template <typename T> int dealias_prepare_T(const HostPlan &, const DevicePtrs &, cudaStream_t);
 template <typename T> int axis0_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
 template <typename T> int products_T(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
+template <typename T> int sep_planes_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
+template <typename T> int fused_T(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
 template <typename T> int dealias_finish_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
 
 int moments_partials_count(const HostPlan &) { return 256; }
@@ -59,6 +61,7 @@ struct wke_plan {
     DevicePtrs dp{};
     void *Hbuf[2] = {nullptr, nullptr};   // double-buffered chunk intermediates
     void *Vbuf[2] = {nullptr, nullptr};   // double-buffered chunk Nyquist tables
+    void *Sbuf[2] = {nullptr, nullptr};   // double-buffered pair planes (separable plans)
     // pass 1 of chunk c+1 runs on s1 while pass 2 of chunk c runs on s2; the
     // Nyquist tables of each chunk are built on s3
     cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
@@ -214,6 +217,14 @@ template <typename T> int upload_tables(wke_plan *p) {
     if ((e = cudaMemcpy(const_cast<double *>(p->dp.prod_W), hp.prod_W.data(), hp.prod_W.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "weight upload");
+    if (hp.separable) {
+        const std::pair<const std::vector<int> *, const int *> tabs[3] = {
+            {&hp.sep_v, p->dp.sep_v}, {&hp.sep_p, p->dp.sep_p}, {&hp.field_pair, p->dp.field_pair}};
+        for (const auto &tb : tabs)
+            if ((e = cudaMemcpy(const_cast<int *>(tb.second), tb.first->data(), tb.first->size() * sizeof(int),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "separable table upload");
+    }
     if (hp.shared) {
         std::vector<int> gc(hp.group_cfield);
         if ((e = cudaMemcpy(const_cast<int *>(p->dp.group_cfield), gc.data(), gc.size() * sizeof(int),
@@ -276,7 +287,7 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
     DevicePtrs dp = p->dp;
     dp.f = f;
     dp.H = p->Hbuf[0];
-    dp.fwd_tmp = p->Hbuf[0];
+    dp.S = p->Sbuf[0];
     // while profiling, both passes share one stream so that each launch's
     // interval measures that kernel alone
     cudaStream_t s1 = p->s1, s2 = p->profiling ? p->s1 : p->s2, s3 = p->profiling ? p->s1 : p->s3;
@@ -298,6 +309,7 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         const int buf = c & 1;
         dp.H = p->Hbuf[buf];
         dp.V = p->Vbuf[buf];
+        dp.S = p->Sbuf[buf];
         if (nyq) {
             // tables of chunk c on s3, once pass 2 of chunk c-2 has read the buffer
             if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s3, p->ev_p2[buf], 0);
@@ -310,9 +322,9 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         if (c >= 2 && !e) e = (int)cudaStreamWaitEvent(s1, p->ev_p2[buf], 0);
         if (!e) {
             ProfScope ps(p, s1, 1);
-            e = pass1_T<T>(hp, dp, c, s1);
+            e = hp.separable ? sep_planes_T<T>(hp, dp, c, s1) : pass1_T<T>(hp, dp, c, s1);
         }
-        if (hp.shared && !e) {            // shared-field layout: axis 0 in place, then the product pass
+        if (hp.shared && !hp.fused && !e) {   // shared-field layout: axis 0 into H, then the product pass
             ProfScope ps(p, s1, 5);
             e = axis0_T<T>(hp, dp, c, s1);
         }
@@ -321,7 +333,8 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         if (!e && nyq) e = (int)cudaStreamWaitEvent(s2, p->ev_nq[buf], 0);
         if (!e) {
             ProfScope ps(p, s2, 2);
-            e = hp.shared ? products_T<T>(hp, dp, c, im, s2) : pass2_T<T>(hp, dp, c, im, s2);
+            e = hp.fused ? fused_T<T>(hp, dp, c, im, s2)
+                : hp.shared ? products_T<T>(hp, dp, c, im, s2) : pass2_T<T>(hp, dp, c, im, s2);
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p2[buf], s2);
     }
@@ -445,13 +458,24 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
     } while (0)
     ALLOC(p->dp.ghat, nd * cxb);
     ALLOC(p->dp.nslice, (size_t)hp.d * (nd / hp.N) * cxb);
-    ALLOC(p->Hbuf[0], chunk_unit_bytes(hp));
-    ALLOC(p->Hbuf[1], chunk_unit_bytes(hp));
+    if (needs_unit_buffers(hp)) {
+        ALLOC(p->Hbuf[0], chunk_unit_bytes(hp));
+        ALLOC(p->Hbuf[1], chunk_unit_bytes(hp));
+    }
+    if (hp.separable) {                   // S[0] also serves as the forward scratch (N^d complex double)
+        ALLOC(p->Sbuf[0], std::max(chunk_s_bytes(hp), nd * 16));
+        ALLOC(p->Sbuf[1], std::max(chunk_s_bytes(hp), nd * 16));
+        ALLOC(p->dp.sep_v, hp.sep_v.size() * sizeof(int));
+        ALLOC(p->dp.sep_p, hp.sep_p.size() * sizeof(int));
+        ALLOC(p->dp.field_pair, hp.field_pair.size() * sizeof(int));
+    }
     if (hp.nyquist == WKE_NYQ_KEEP) {
         ALLOC(p->Vbuf[0], chunk_v_bytes(hp));
         ALLOC(p->Vbuf[1], chunk_v_bytes(hp));
     }
-    p->dp.H = p->dp.fwd_tmp = p->Hbuf[0];
+    p->dp.H = p->Hbuf[0];
+    p->dp.S = p->Sbuf[0];
+    p->dp.fwd_tmp = needs_unit_buffers(hp) ? p->Hbuf[0] : p->Sbuf[0];
     ALLOC(p->dp.Qacc, (size_t)n_accumulators(hp) * nd * 8);
     ALLOC(p->dp.Qacc_im, (size_t)n_accumulators(hp) * nd * 8);
     ALLOC(p->dp.group_cfield, (size_t)hp.n_groups * sizeof(int));
@@ -526,11 +550,10 @@ static void fill_info(const HostPlan &hp, wke_plan_info *info) {
     info->products_per_group = hp.products_per_group;
     info->groups_per_chunk = hp.groups_per_chunk;
     info->n_chunks = hp.n_chunks;
-    // forward: one line kernel per axis; per chunk pass 1, (Nyquist tables), pass 2 or
-    // axis 0 + products; finalize
-    info->launches_per_collision = hp.d + (hp.nyquist == WKE_NYQ_KEEP ? 3 : 2) * hp.n_chunks + 1 +
-                                   (hp.shared ? hp.n_chunks : 0) +
-                                   (hp.dealias ? 1 + 2 * hp.d : 0);
+    info->launches_per_collision = launches_per_collision(hp);
+    info->separable = hp.separable ? 1 : 0;
+    info->pair_planes_per_collision = hp.separable ? hp.chunk_p0.back() : 0;
+    info->fused_products = hp.fused ? 1 : 0;
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
 }

@@ -73,6 +73,26 @@ struct HostPlan {
     int max_chunk_fields = 0;
     int n_fields_total = 0;               // rows of the phase table
 
+    // Separable transforms (3D, shared-field layout).  The phase of a field
+    // with shift x factors per axis, exp(-i pi j.x / L) = E0(j1, x0) E1(j2, x1)
+    // E2(j3, x2), so the inverse transform of ghat E_x over axis 2 depends on
+    // x2 alone and the one over axes 1 and 2 on (x1, x2) alone; only the
+    // axis-0 transform is per field.  Per chunk the distinct x2 values
+    // ("row values") and the distinct (x1, x2) pairs are listed, the pairs
+    // grouped by row value; the trailing-axis pass transforms each row value
+    // and each pair once per plane, and each unit's axis-0 transform starts
+    // from the pair planes of its two fields.
+    bool separable = false;
+    std::vector<int> chunk_v0, chunk_p0;  // n_chunks + 1: first row value / first pair of each chunk
+    std::vector<int> sep_v;               // per row value: a field with that x2 (global id), first
+                                          // and end pair (chunk-local), 3 ints each
+    std::vector<int> sep_p;               // per pair: a field with that (x1, x2) (global id)
+    std::vector<int> field_pair;          // per field: its pair (chunk-local)
+    int max_chunk_pairs = 0, max_chunk_values = 0;
+    // The product pass of the shared layout fused with the axis-0 transform
+    // (3D, FP32, not split): no unit buffer between them.
+    bool fused = false;
+
     double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)
 
     // Launch layout (wke_plan_set_tuning / wke_plan_autotune).
@@ -119,6 +139,11 @@ struct DevicePtrs {
     const void *Kproj;        // N_in x N complex double: projection onto modes [-N_in/2, N_in/2-1]
     const int *prod_local;    // n_groups * products_per_group * 2 ints: local fields (fa, fb)
     const int *group_cfield;  // shared-field layout: chunk-local C field of each group
+    // separable transforms
+    void *S;                  // chunk pair planes: max_chunk_pairs * N^3 complex T
+    const int *sep_v;         // 3 ints per row value (HostPlan::sep_v)
+    const int *sep_p;         // per pair: field for the axis-1 phase row
+    const int *field_pair;    // per field: chunk-local pair
     const double *prod_W;     // n_groups * products_per_group
 };
 
@@ -138,6 +163,14 @@ inline int max_chunk_units(const HostPlan &hp) {
 }
 size_t chunk_unit_bytes(const HostPlan &hp);   // H buffer bytes for a full chunk
 size_t chunk_v_bytes(const HostPlan &hp);      // V buffer bytes for a full chunk
+size_t chunk_s_bytes(const HostPlan &hp);      // S buffer bytes for a full chunk (separable plans)
+int launches_per_collision(const HostPlan &hp);
+// The unit buffers H: the output of pass 1 (per-unit transforms) or of the
+// separate axis-0 pass; a separable plan whose axis-0 transform is fused
+// with the products has none.
+inline bool needs_unit_buffers(const HostPlan &hp) { return !(hp.separable && hp.fused); }
+// Dynamic shared memory of the fused axis-0 + product kernel (3D FP32).
+size_t fused_smem_bytes(int N, int K);
 
 int launch_forward(const HostPlan &hp, const DevicePtrs &p, void *stream);
 int launch_pass1(const HostPlan &hp, const DevicePtrs &p, int g0, int ng, void *stream);

@@ -299,6 +299,56 @@ k_pass1_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T
     }
 }
 
+// Separable trailing-axis pass (3D; HostPlan::separable).  Block (j1, row
+// value vi of the chunk): the rows of plane j1 of ghat times E2(j3, x2) of
+// the row value are transformed along axis 2 once (warp lines, into `work`),
+// then for every pair (x1, x2) of that row value the columns of the result
+// times E1(j2, x1) are transformed along axis 1 (column lines, 32
+// consecutive columns per warp) into the pair's plane S[pair][j1][.][.].
+// The axis-0 phase E0(j1, x0) of each field is applied by the axis-0 pass.
+// sep_v[3 v] = field of row value v (its axis-2 phase row), [3 v + 1],
+// [3 v + 2] = first and end pair (chunk-local); sep_p[p] = field of pair p
+// (its axis-1 phase row); v0 / p0 = the chunk's first row value / pair.
+template <typename T, int N>
+__global__ void __launch_bounds__(N * LineCfg<T, N>::TPL)
+k_sep_planes_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase, cx<T> *__restrict__ S,
+                const cx<T> *__restrict__ tw_g, const int *__restrict__ sep_v, const int *__restrict__ sep_p, int v0,
+                int p0) {
+    typedef LineCfg<T, N> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW, WP = Work<N>::PITCH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *work = tw + N;
+    cx<T> *scratch = work + N * WP;           // row scratch, then column scratch
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = lane % LPW, t = lane / LPW;
+    const int row = warp * LPW + c;           // j2 of this row line
+    const int z = threadIdx.x % N, ty = threadIdx.x / N;   // column lines
+    const int j1 = blockIdx.x, v = v0 + blockIdx.y;
+    const int vf = sep_v[3 * v], pb = sep_v[3 * v + 1], pe = sep_v[3 * v + 2];
+    const cx<T> *grow = ghat + ((size_t)j1 * N + row) * N;
+    const cx<T> *e2 = phase + (size_t)vf * 3 * N + 2 * N;
+    cx<T> x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmul<T>(grow[t + e * TPL], e2[t + e * TPL]);
+    twiddle_store<T, N>(tw, twv, tw_g);
+    line_fft<T, N, E, +1>(x, t, scratch + (size_t)row * LinePad<N>::PITCH, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) work[row * WP + t + e * TPL] = x[e];
+    __syncthreads();
+    const size_t NN = (size_t)N * N;
+    for (int p = pb; p < pe; ++p) {
+        const cx<T> *e1 = phase + (size_t)sep_p[p0 + p] * 3 * N + N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = cmul<T>(work[(ty + e * TPL) * WP + z], e1[ty + e * TPL]);
+        col_fft<T, N, E, +1>(x, ty, scratch, z, N, tw);
+        cx<T> *out = S + ((size_t)p * N + j1) * NN;
+#pragma unroll
+        for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = x[e];
+    }
+}
+
 // 2D: block (row block, unit).  Row j1 of the packed spectrum, inverse
 // transform along axis 1 -> H[unit][j1][y].
 template <typename T, int N>
@@ -683,6 +733,50 @@ k_axis0(cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB) {
     for (int e = 0; e < E; ++e) Hu[(size_t)(t + e * TPL) * P] = v[e];
 }
 
+// Separable plans: the axis-0 input of unit u (fields a, b) from the pair
+// planes, E0(j1, x0a) S_a(j1, col) + i E0(j1, x0b) S_b(j1, col), the packed
+// spectrum's transform over the trailing axes (exact: the phases factor per
+// axis).  `fb` < 0 for a lone field.
+template <typename T>
+__device__ __forceinline__ cx<T> sep_input(const cx<T> *__restrict__ sa, const cx<T> *__restrict__ sb,
+                                           const cx<T> *__restrict__ ea, const cx<T> *__restrict__ eb, int j1,
+                                           size_t stride, bool pair) {
+    const cx<T> A = cmul<T>(sa[(size_t)j1 * stride], ea[j1]);
+    if (!pair) return A;
+    const cx<T> B = cmul<T>(sb[(size_t)j1 * stride], eb[j1]);
+    return mkc<T>(A.x - B.y, A.y + B.x);
+}
+
+// Axis-0 transform of every unit of a separable chunk, from the pair planes
+// into H (the layout k_axis0 leaves).  Block (column tile, unit).
+template <typename T, int N, int EP>
+__global__ void __launch_bounds__(Pass2Cfg<T, N, EP>::THREADS)
+k_axis0_sep(const cx<T> *__restrict__ S, const cx<T> *__restrict__ phase, const int *__restrict__ field_pair,
+            cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB, int sf0, int K) {
+    typedef Pass2Cfg<T, N, EP> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *scratch = tw + N;                  // LinePad<N>::LEN rows x CB columns
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
+    const int z = threadIdx.x % CB, t = threadIdx.x / CB;
+    const int col = blockIdx.x * CB + z;
+    const int u = blockIdx.y, fa = sf0 + 2 * u;
+    const bool pair = 2 * u + 1 < K;
+    const int fb = pair ? fa + 1 : fa;
+    const size_t ND = (size_t)N * P;
+    const cx<T> *sa = S + (size_t)field_pair[fa] * ND + col, *sb = S + (size_t)field_pair[fb] * ND + col;
+    const cx<T> *ea = phase + (size_t)fa * 3 * N, *eb = phase + (size_t)fb * 3 * N;
+    cx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = sep_input<T>(sa, sb, ea, eb, t + e * TPL, P, pair);
+    twiddle_store<T, N>(tw, twv, tw_g);
+    col_fft<T, N, E, +1>(v, t, scratch, z, CB, tw);
+    cx<T> *Hu = H + (size_t)u * ND + col;
+#pragma unroll
+    for (int e = 0; e < E; ++e) Hu[(size_t)(t + e * TPL) * P] = v[e];
+}
+
 // Split-precision axis-0 transform on the tensor cores (WKE_SPLIT).  The
 // inverse N-point DFT of every column of a tile of CB = 32 columns is the
 // real GEMM
@@ -1014,6 +1108,126 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
             const T ur = Sab.x, ui = Sab.y;
             acc += e.w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
             if (IM) acci += e.w * ((pr * si + pim * sr) - (cr * ui + ci * ur));
+        }
+        T tsum = sum + acc;
+        comp += fabs(sum) >= fabs(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+        sum = tsum;
+        if (IM) {
+            tsum = sumi + acci;
+            compi += fabs(sumi) >= fabs(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+            sumi = tsum;
+        }
+    }
+    Qacc[idx] += (double)sum + (double)comp;
+    if (IM) Qim[idx] += (double)sumi + (double)compi;
+}
+
+// Fused axis-0 transform and product pass (3D, FP32, shared-field layout).
+// Block: CB = LPW consecutive columns of one i2 row (LPW = lines per warp of
+// the warp-line transform), all N points of each along axis 0, so N * CB
+// points and as many threads.  Each warp takes whole units: its lanes hold
+// the CB columns' lines (lane = column + CB * t), it forms the unit's axis-0
+// input (the pass-1 output, or for separable plans E0a S_a + i E0b S_b from
+// the pair planes), transforms it with the warp-local Stockham line
+// (exchanges through the warp's own padded scratch, __syncwarp only), adds
+// the Nyquist imaginary parts and writes the unit's two fields at its points
+// into the block's field slots.  After one barrier every thread forms, at
+// its point, the products of all groups of the chunk from the field slots,
+// with the same algebra and summation order as k_products_staged.  The
+// chunk's product table arrives as a kernel parameter.
+template <typename T> struct FusedTab {
+    static constexpr int kMaxProducts = 256, kMaxGroups = 64;
+    unsigned char pa[kMaxProducts], pb[kMaxProducts];   // chunk-local field ids
+    unsigned char cf[kMaxGroups];                       // C field of each group
+    T w[kMaxProducts];
+};
+
+template <typename T, int N, bool SEP, bool IM, bool NYQ, int PPGC>
+__global__ void __launch_bounds__(N * LineCfg<T, N>::LPW)
+k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const int *__restrict__ field_pair,
+           const cx<T> *__restrict__ Vtab, const T *__restrict__ f, double *__restrict__ Qacc,
+           double *__restrict__ Qim, const cx<T> *__restrict__ tw_g, int sf0, int K, int ng, int PPG,
+           const __grid_constant__ FusedTab<T> tab) {
+    typedef LineCfg<T, N> Cfg;
+    constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
+    constexpr int CB = LPW, PTS = N * CB, WARPS = PTS / 32;
+    constexpr int P = N * N;
+    constexpr size_t ND = (size_t)N * P;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *fld = tw + N;                                   // field k at point pt: fld[k * PTS + pt]
+    cx<T> *scr = fld + (size_t)K * PTS;                    // WARPS * LPW lines of LinePad<N>::PITCH
+    const cx<T> twv = twiddle_fetch<T, N>(tw_g);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = lane % LPW, t = lane / LPW;
+    const int col0 = blockIdx.x * CB;
+    const int i2 = col0 / N, i3 = col0 - i2 * N + c;      // this lane's column (transform phase)
+    const int col = col0 + c;
+    const int U = (K + 1) / 2;
+    twiddle_store<T, N>(tw, twv, tw_g);
+    cx<T> *wscr = scr + (size_t)(warp * LPW + c) * LinePad<N>::PITCH;
+    const T sgn1 = (t & 1) ? (T)-1 : (T)1;               // (-1)^{i1}: TPL is even
+    const T s2 = (i2 & 1) ? (T)-1 : (T)1, s3 = (i3 & 1) ? (T)-1 : (T)1;
+    for (int u = warp; u < U; u += WARPS) {
+        const int fa = sf0 + 2 * u;
+        const bool pair = 2 * u + 1 < K;
+        cx<T> v[E];
+        if (SEP) {
+            const int fb = pair ? fa + 1 : fa;
+            const cx<T> *sa = src + (size_t)field_pair[fa] * ND + col, *sb = src + (size_t)field_pair[fb] * ND + col;
+            const cx<T> *ea = phase + (size_t)fa * 3 * N, *eb = phase + (size_t)fb * 3 * N;
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = sep_input<T>(sa, sb, ea, eb, t + e * TPL, P, pair);
+        } else {
+            const cx<T> *hu = src + (size_t)u * ND + col;
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = hu[(size_t)(t + e * TPL) * P];
+        }
+        // Nyquist imaginary parts (a of the real-slot field, b of the other)
+        cx<T> nq[E];
+        if (NYQ) {
+            const cx<T> *Vu = Vtab + (size_t)u * 3 * P;
+            const cx<T> v0 = Vu[col];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i1 = t + e * TPL;
+                const cx<T> v1 = Vu[P + i1 * N + i3], v2 = Vu[2 * P + i1 * N + i2];
+                nq[e] = mkc<T>(sgn1 * v0.x + s2 * v1.x + s3 * v2.x, sgn1 * v0.y + s2 * v1.y + s3 * v2.y);
+            }
+        }
+        line_fft<T, N, E, +1>(v, t, wscr, tw);
+        cx<T> *fa_s = fld + (size_t)(2 * u) * PTS + c;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int pt = (t + e * TPL) * CB;
+            const T a = NYQ ? nq[e].x : (T)0, b = NYQ ? nq[e].y : (T)0;
+            fa_s[pt] = mkc<T>(v[e].x + b, a);
+            if (pair) fa_s[PTS + pt] = mkc<T>(v[e].y - a, b);
+        }
+    }
+    __syncthreads();
+    // products at this thread's point
+    const int pt = threadIdx.x;
+    const int i1 = pt / CB, zc = pt - i1 * CB;
+    const size_t idx = (size_t)i1 * P + col0 + zc;
+    const cx<T> *fb = fld + pt;
+    const T F = f[idx];
+    const int ppg = PPGC > 0 ? PPGC : PPG;
+    T sum = (T)0, comp = (T)0, sumi = (T)0, compi = (T)0;
+    int k = 0;
+    for (int g = 0; g < ng; ++g) {
+        const cx<T> C = fb[(int)tab.cf[g] * PTS];
+        const T sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
+        T acc = (T)0, acci = (T)0;
+#pragma unroll
+        for (int p = 0; p < ppg; ++p, ++k) {
+            const cx<T> A = fb[(int)tab.pa[k] * PTS], Bf = fb[(int)tab.pb[k] * PTS];
+            const T w = tab.w[k];
+            const T pr = A.x * Bf.x - A.y * Bf.y, pim = A.x * Bf.y + A.y * Bf.x;   // A B
+            const cx<T> Sab = cadd<T>(A, Bf);                                      // A + B
+            const T ur = Sab.x, ui = Sab.y;
+            acc += w * ((pr * sr - pim * si) - (cr * ur - ci * ui));
+            if (IM) acci += w * ((pr * si + pim * sr) - (cr * ui + ci * ur));
         }
         T tsum = sum + acc;
         comp += fabs(sum) >= fabs(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;

@@ -165,6 +165,24 @@ static int pass1_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t 
     return (int)cudaGetLastError();
 }
 
+// Separable plans: the chunk's row values and pairs along axes 2 and 1 into S.
+template <typename T, int N>
+static int sep_planes_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    typedef LineCfg<T, N> Cfg;
+    if constexpr (N <= 64) {
+        const int v0 = hp.chunk_v0[c], nv = hp.chunk_v0[c + 1] - v0;
+        const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
+        int rc = 0;
+        if ((rc = set_smem(k_sep_planes_3d<T, N>, smem))) return rc;
+        k_sep_planes_3d<T, N><<<dim3(N, nv), N * Cfg::TPL, smem, s>>>(
+            static_cast<const cx<T> *>(p.ghat), static_cast<const cx<T> *>(p.phase), static_cast<cx<T> *>(p.S),
+            static_cast<const cx<T> *>(p.tw), p.sep_v, p.sep_p, v0, hp.chunk_p0[c]);
+        return (int)cudaGetLastError();
+    } else {
+        return (int)cudaErrorInvalidValue;
+    }
+}
+
 // ------------------------------------------------------------------ Nyquist tables
 // Tables of every unit of chunk c, into p.V.
 template <typename T, int N>
@@ -211,7 +229,33 @@ template <typename T, int N, int EP> static int axis0_ne(const HostPlan &hp, con
     return (int)cudaGetLastError();
 }
 
+template <typename T, int N, int EP>
+static int axis0_sep_ne(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    typedef Pass2Cfg<T, N, EP> Cfg;
+    const ChunkRange cr = chunk_range(hp, c);
+    const int P = cols_of(hp);
+    int CB = std::min(Cfg::CB, P);
+    while (P % CB) CB /= 2;
+    const size_t smem = (size_t)(N + LinePad<N>::LEN * CB) * sizeof(cx<T>);
+    int rc = 0;
+    if ((rc = set_smem(k_axis0_sep<T, N, EP>, smem))) return rc;
+    k_axis0_sep<T, N, EP><<<dim3(P / CB, cr.units), CB * Cfg::TPL, smem, s>>>(
+        static_cast<const cx<T> *>(p.S), static_cast<const cx<T> *>(p.phase), p.field_pair, static_cast<cx<T> *>(p.H),
+        static_cast<const cx<T> *>(p.tw), P, CB, cr.sf0, cr.sK);
+    return (int)cudaGetLastError();
+}
+
 template <typename T, int N> static int axis0_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    if (hp.separable) {
+        if constexpr (N % 3 == 0) {
+            return axis0_sep_ne<T, N, 12>(hp, p, c, s);
+        } else {
+            if constexpr (N <= 64) {
+                if (hp.tune_p2_points == 8) return axis0_sep_ne<T, N, 8>(hp, p, c, s);
+            }
+            return axis0_sep_ne<T, N, 4>(hp, p, c, s);
+        }
+    }
     if constexpr (N % 3 == 0) {
         return axis0_ne<T, N, 12>(hp, p, c, s);
     } else {
@@ -219,6 +263,60 @@ template <typename T, int N> static int axis0_n(const HostPlan &hp, const Device
             if (hp.tune_p2_points == 8) return axis0_ne<T, N, 8>(hp, p, c, s);
         }
         return axis0_ne<T, N, 4>(hp, p, c, s);
+    }
+}
+
+// ------------------------------------------------------------------ fused axis 0 + products
+template <typename T, int N, bool SEP, bool IM, bool NYQ, int PPGC>
+static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    typedef LineCfg<T, N> Cfg;
+    constexpr int CB = Cfg::LPW, PTS = N * CB;
+    const ChunkRange cr = chunk_range(hp, c);
+    FusedTab<T> tab;
+    const int np = cr.ng * hp.products_per_group;
+    if (np > FusedTab<T>::kMaxProducts || cr.ng > FusedTab<T>::kMaxGroups || cr.sK > 255)
+        return (int)cudaErrorInvalidValue;
+    for (int i = 0; i < np; ++i) {
+        const int slot = cr.g0 * hp.products_per_group + i;
+        tab.pa[i] = (unsigned char)hp.prod_fa[slot];
+        tab.pb[i] = (unsigned char)hp.prod_fb[slot];
+        tab.w[i] = (T)hp.prod_W[slot];
+    }
+    for (int g = 0; g < cr.ng; ++g) tab.cf[g] = (unsigned char)hp.group_cfield[cr.g0 + g];
+    const size_t smem = fused_smem_bytes(N, cr.sK);
+    int rc = 0;
+    if ((rc = set_smem(k_fused_3d<T, N, SEP, IM, NYQ, PPGC>, smem))) return rc;
+    k_fused_3d<T, N, SEP, IM, NYQ, PPGC><<<(N * N) / CB, PTS, smem, s>>>(
+        static_cast<const cx<T> *>(SEP ? p.S : p.H), static_cast<const cx<T> *>(p.phase), p.field_pair,
+        static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc, p.Qacc_im,
+        static_cast<const cx<T> *>(p.tw), cr.sf0, cr.sK, cr.ng, hp.products_per_group, tab);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int N, bool SEP, bool IM, bool NYQ>
+static int fused_nim(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    switch (hp.products_per_group) {
+    case 1: return fused_nimp<T, N, SEP, IM, NYQ, 1>(hp, p, c, s);
+    case 2: return fused_nimp<T, N, SEP, IM, NYQ, 2>(hp, p, c, s);
+    case 3: return fused_nimp<T, N, SEP, IM, NYQ, 3>(hp, p, c, s);
+    case 4: return fused_nimp<T, N, SEP, IM, NYQ, 4>(hp, p, c, s);
+    default: return fused_nimp<T, N, SEP, IM, NYQ, 0>(hp, p, c, s);
+    }
+}
+
+template <typename T, int N, bool SEP>
+static int fused_ns(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
+    const bool nyq = hp.nyquist == WKE_NYQ_KEEP;
+    if (nyq) return im ? fused_nim<T, N, SEP, true, true>(hp, p, c, s) : fused_nim<T, N, SEP, false, true>(hp, p, c, s);
+    return im ? fused_nim<T, N, SEP, true, false>(hp, p, c, s) : fused_nim<T, N, SEP, false, false>(hp, p, c, s);
+}
+
+template <typename T, int N>
+static int fused_n(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && N <= 64) {
+        return hp.separable ? fused_ns<T, N, true>(hp, p, c, im, s) : fused_ns<T, N, false>(hp, p, c, im, s);
+    } else {
+        return (int)cudaErrorInvalidValue;
     }
 }
 
@@ -404,6 +502,26 @@ template <typename T> int axis0_T(const HostPlan &hp, const DevicePtrs &p, int c
     return (int)cudaErrorInvalidValue;
 }
 
+template <typename T> int sep_planes_T(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return sep_planes_n<T, 16>(hp, p, c, s);
+        case 32: return sep_planes_n<T, 32>(hp, p, c, s);
+        case 48: return sep_planes_n<T, 48>(hp, p, c, s);
+        case 64: return sep_planes_n<T, 64>(hp, p, c, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <typename T> int fused_T(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
+    switch (hp.N) {
+        case 16: return fused_n<T, 16>(hp, p, c, im, s);
+        case 32: return fused_n<T, 32>(hp, p, c, im, s);
+        case 48: return fused_n<T, 48>(hp, p, c, im, s);
+        case 64: return fused_n<T, 64>(hp, p, c, im, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
 template <typename T>
 int finalize_T(const HostPlan &hp, const DevicePtrs &p, void *Q, void *Qim, cudaStream_t s) {
     const size_t ND = nd_of(hp);
@@ -510,6 +628,8 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);                \
     template int axis0_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                      \
     template int products_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);             \
+    template int sep_planes_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                 \
+    template int fused_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);                \
     template int finalize_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);        \
     template int moments_T<T>(const HostPlan &, const void *, double *, double *, cudaStream_t);           \
     template int rk_stage_T<T>(const HostPlan &, const void *, const void *, double *, void *, double,     \

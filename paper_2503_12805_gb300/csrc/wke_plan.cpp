@@ -316,6 +316,85 @@ static int build_shared_layout(HostPlan &hp, bool force) {
     return WKE_OK;
 }
 
+// Separable transforms (3D, shared-field layout; see HostPlan::separable).
+// Row values and pairs are equal when they agree to 1e-12 (relative), as
+// fields are; the first field with a value supplies its phase row.  With
+// `force` false the layout is kept when the row-value and pair transforms
+// are at most 85% of the two trailing-axis transforms of every unit.
+static int build_separable(HostPlan &hp, bool force) {
+    const int d = hp.d;
+    std::vector<int> chunk_v0{0}, chunk_p0{0}, sep_v, sep_p, field_pair(hp.n_fields_total, 0);
+    double sep_cost = 0.0, unit_cost = 0.0;
+    int maxp = 0, maxv = 0;
+    auto same = [](double a, double b) { return std::fabs(a - b) <= 1e-12 * (1.0 + std::fabs(a)); };
+    for (int c = 0; c < hp.n_chunks; ++c) {
+        const int f0 = hp.chunk_f0[c], f1 = hp.chunk_f0[c + 1];
+        std::vector<int> vrep;                     // field of each row value
+        std::vector<std::vector<int>> prep;        // per row value: field of each pair
+        std::vector<int> fv(f1 - f0), fp(f1 - f0);
+        for (int f = f0; f < f1; ++f) {
+            const double *x = &hp.field_shift[(size_t)f * d];
+            int vi = -1;
+            for (size_t k = 0; k < vrep.size() && vi < 0; ++k)
+                if (same(hp.field_shift[(size_t)vrep[k] * d + 2], x[2])) vi = (int)k;
+            if (vi < 0) {
+                vi = (int)vrep.size();
+                vrep.push_back(f);
+                prep.emplace_back();
+            }
+            int pi = -1;
+            for (size_t k = 0; k < prep[vi].size() && pi < 0; ++k)
+                if (same(hp.field_shift[(size_t)prep[vi][k] * d + 1], x[1])) pi = (int)k;
+            if (pi < 0) {
+                pi = (int)prep[vi].size();
+                prep[vi].push_back(f);
+            }
+            fv[f - f0] = vi;
+            fp[f - f0] = pi;
+        }
+        std::vector<int> first(vrep.size() + 1, 0);
+        for (size_t k = 0; k < vrep.size(); ++k) first[k + 1] = first[k] + (int)prep[k].size();
+        for (size_t k = 0; k < vrep.size(); ++k) {
+            sep_v.push_back(vrep[k]);
+            sep_v.push_back(first[k]);
+            sep_v.push_back(first[k + 1]);
+            for (int pf : prep[k]) sep_p.push_back(pf);
+        }
+        for (int f = f0; f < f1; ++f) field_pair[f] = first[fv[f - f0]] + fp[f - f0];
+        chunk_v0.push_back((int)(sep_v.size() / 3));
+        chunk_p0.push_back((int)sep_p.size());
+        maxv = std::max(maxv, (int)vrep.size());
+        maxp = std::max(maxp, first.back());
+        sep_cost += (double)vrep.size() + first.back();
+        unit_cost += 2.0 * ((f1 - f0 + 1) / 2);
+    }
+    if (!force && sep_cost > 0.85 * unit_cost) return WKE_OK;
+    hp.separable = true;
+    hp.chunk_v0 = chunk_v0;
+    hp.chunk_p0 = chunk_p0;
+    hp.sep_v = sep_v;
+    hp.sep_p = sep_p;
+    hp.field_pair = field_pair;
+    hp.max_chunk_pairs = maxp;
+    hp.max_chunk_values = maxv;
+    return WKE_OK;
+}
+
+// Product-pass limits of the fused axis-0 + product kernel: the chunk's
+// product table travels as a kernel parameter.
+constexpr int kFusedMaxProducts = 256, kFusedMaxGroups = 64;
+
+// Dynamic shared memory of the fused kernel for a 3D FP32 transform grid N
+// and K fields: twiddles, K field slots of the block's N * LPW points and a
+// padded exchange line for each line of each warp (LineCfg / LinePad of the
+// kernels: 8 points per thread, 12 for N = 48).
+size_t fused_smem_bytes(int N, int K) {
+    const int E = N % 3 == 0 ? 12 : 8, TPL = N / E, LPW = 32 / TPL;
+    const int len = N + N / 8, pitch = len + ((4 - (len % 16)) + 16) % 16;
+    const int pts = N * LPW, warps = pts / 32;
+    return (size_t)(N + (size_t)K * pts + (size_t)warps * LPW * pitch) * 8;
+}
+
 int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, HostPlan &hp) {
     if (!quad) return fail(WKE_ERR_INVALID, "quadrature descriptor is NULL");
     if (d != 2 && d != 3) return fail(WKE_ERR_INVALID, "d must be 2 or 3");
@@ -525,14 +604,29 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     hp.n_chunks = (hp.n_groups + hp.groups_per_chunk - 1) / hp.groups_per_chunk;
     hp.n_fields_total = hp.n_groups * hp.fields_per_group;
 
-    if (quad->layout != WKE_LAYOUT_AUTO && quad->layout != WKE_LAYOUT_PER_GROUP && quad->layout != WKE_LAYOUT_SHARED)
-        return fail(WKE_ERR_INVALID, "layout must be WKE_LAYOUT_AUTO, _PER_GROUP or _SHARED");
+    if (quad->layout != WKE_LAYOUT_AUTO && quad->layout != WKE_LAYOUT_PER_GROUP && quad->layout != WKE_LAYOUT_SHARED &&
+        quad->layout != WKE_LAYOUT_SEPARABLE)
+        return fail(WKE_ERR_INVALID, "layout must be WKE_LAYOUT_AUTO, _PER_GROUP, _SHARED or _SEPARABLE");
+    if (quad->layout == WKE_LAYOUT_SEPARABLE && (d != 3 || hp.split))
+        return fail(WKE_ERR_INVALID, "WKE_LAYOUT_SEPARABLE needs d = 3 and is not available with WKE_SPLIT");
     if (quad->layout != WKE_LAYOUT_PER_GROUP) {
-        int rc2 = build_shared_layout(hp, quad->layout == WKE_LAYOUT_SHARED || hp.split);
+        int rc2 = build_shared_layout(hp, quad->layout == WKE_LAYOUT_SHARED || quad->layout == WKE_LAYOUT_SEPARABLE ||
+                                              hp.split);
         if (rc2) return rc2;
     }
     if (hp.split && (d != 3 || (hp.N != 32 && hp.N != 64)))
         return fail(WKE_ERR_UNSUPPORTED, "WKE_SPLIT is built for 3D transform grids of N = 32 or 64");
+    if (hp.shared && d == 3 && !hp.split && quad->layout != WKE_LAYOUT_SHARED) {
+        int rc2 = build_separable(hp, quad->layout == WKE_LAYOUT_SEPARABLE);
+        if (rc2) return rc2;
+    }
+    if (hp.shared && d == 3 && hp.precision == WKE_FP32 && !hp.split) {
+        int maxp = 0;
+        for (int c = 0; c < hp.n_chunks; ++c)
+            maxp = std::max(maxp, (hp.chunk_g0[c + 1] - hp.chunk_g0[c]) * hp.products_per_group);
+        hp.fused = hp.groups_per_chunk <= kFusedMaxGroups && maxp <= kFusedMaxProducts &&
+                   hp.max_chunk_fields <= 255 && fused_smem_bytes(hp.N, hp.max_chunk_fields) <= 227 * 1024;
+    }
 
     hp.scale = std::ldexp(1.0, 1 - d) * (hp.dispersion == WKE_OMEGA_K2 ? 0.5 : 1.0);
     return WKE_OK;
@@ -559,6 +653,23 @@ size_t chunk_v_bytes(const HostPlan &hp) {
     return (size_t)max_chunk_units(hp) * hp.d * (grid_size(hp) / hp.N) * cxb;
 }
 
+size_t chunk_s_bytes(const HostPlan &hp) {
+    size_t cxb = hp.precision == WKE_FP64 ? 16 : 8;
+    return (size_t)hp.max_chunk_pairs * grid_size(hp) * cxb;
+}
+
+// Kernels one evaluation launches: the forward transform (d line kernels),
+// per chunk the Nyquist tables (Nyquist kept), the trailing-axis pass, the
+// axis-0 transform (shared layout, unless fused with the products) and the
+// product pass, then finalize (de-aliased plans: 1 padding + d maps before,
+// 1 + d maps after instead of finalize).
+int launches_per_collision(const HostPlan &hp) {
+    int per_chunk = (hp.nyquist == WKE_NYQ_KEEP ? 1 : 0) + 2 + (hp.shared && !hp.fused ? 1 : 0);
+    int n = hp.d + per_chunk * hp.n_chunks + 1;
+    if (hp.dealias) n += 1 + hp.d + hp.d;
+    return n;
+}
+
 static size_t grid_size(const HostPlan &hp) {
     size_t nd = 1;
     for (int a = 0; a < hp.d; ++a) nd *= (size_t)hp.N;
@@ -572,7 +683,11 @@ size_t plan_device_bytes(const HostPlan &hp) {
     size_t n_fields = (size_t)hp.n_fields_total;
     size_t bytes = 0;
     bytes += nd * cxb + hp.d * (nd / hp.N) * cxb;                       // ghat, Nyquist slices
-    bytes += 2 * chunk_unit_bytes(hp);                                   // H double-buffered
+    if (needs_unit_buffers(hp)) bytes += 2 * chunk_unit_bytes(hp);     // H double-buffered
+    if (hp.separable) bytes += 2 * std::max(chunk_s_bytes(hp), nd * 16); // S double-buffered (S[0] also
+                                                                        // the forward scratch)
+    if (hp.separable)
+        bytes += (hp.sep_v.size() + hp.sep_p.size() + hp.field_pair.size()) * sizeof(int);
     if (hp.nyquist == WKE_NYQ_KEEP) bytes += 2 * chunk_v_bytes(hp);      // Nyquist tables, double-buffered
     bytes += 2 * (size_t)(hp.shared ? 1 : hp.groups_per_chunk) * nd * 8;   // Qacc, Qacc_im
     bytes += (size_t)hp.n_groups * sizeof(int);                         // C field of each group
@@ -614,6 +729,12 @@ double plan_flops(const HostPlan &hp) {
         fwd += maps;
     }
     double inv = units * 5.0 * nd * lg;                    // pass 1 + pass 2 transforms
+    if (hp.separable) {
+        // trailing axes once per row value (axis 2) and once per pair (axis 1),
+        // axis 0 per unit
+        double vals = (double)(hp.chunk_v0.back()), pairs = (double)(hp.chunk_p0.back());
+        inv = (vals + pairs) * 5.0 * nd * std::log2((double)hp.N) + units * 5.0 * nd * std::log2((double)hp.N);
+    }
     // per-group layout: pass 2 transforms each group's C unit once per group
     double c_again = hp.shared ? 0.0
                                : ((double)hp.n_groups - (units - n_prod)) * 5.0 * nd * std::log2((double)hp.N);
@@ -621,6 +742,8 @@ double plan_flops(const HostPlan &hp) {
     // Nyquist tables: d transforms of N^{d-1} points per unit (two fields each)
     double nyq = hp.nyquist == WKE_NYQ_KEEP ? units * hp.d * 5.0 * (nd / hp.N) * std::log2(nd / hp.N) : 0.0;
     double phases = units * nd * 16.0;                     // two phase products and the packing per point
+    if (hp.separable)                                      // a phase product per row value and pair, two per unit
+        phases = (double)(hp.chunk_v0.back() + hp.chunk_p0.back()) * nd * 6.0 + units * nd * 14.0;
     double prods = n_prod * nd * 30.0;                     // cubic product, weight, accumulate
     return fwd + inv + c_again + nyq + phases + prods;
 }

@@ -37,6 +37,7 @@ WKE_DEALIAS_PAD2 = 1
 WKE_LAYOUT_AUTO = 0
 WKE_LAYOUT_PER_GROUP = 1
 WKE_LAYOUT_SHARED = 2
+WKE_LAYOUT_SEPARABLE = 3
 WKE_OMEGA_HALF_K2 = 0
 WKE_OMEGA_K2 = 1
 
@@ -79,7 +80,8 @@ class WkePlanInfo(ctypes.Structure):
         ("n_chunks", ctypes.c_int), ("launches_per_collision", ctypes.c_int),
         ("flops_per_collision", ctypes.c_double), ("l2_bytes_per_collision", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int), ("shared_fields", ctypes.c_int),
-        ("units_per_collision", ctypes.c_int),
+        ("units_per_collision", ctypes.c_int), ("separable", ctypes.c_int),
+        ("pair_planes_per_collision", ctypes.c_int), ("fused_products", ctypes.c_int),
     ]
 
 
@@ -383,7 +385,8 @@ class Plan:
         q.pair_antipodal = int(pair_antipodal)
         q.chunk_bytes = chunk_bytes
         q.alias = WKE_DEALIAS_PAD2 if dealias else WKE_ALIAS_CIRCULAR
-        q.layout = {"auto": WKE_LAYOUT_AUTO, "per_group": WKE_LAYOUT_PER_GROUP, "shared": WKE_LAYOUT_SHARED}[layout]
+        q.layout = {"auto": WKE_LAYOUT_AUTO, "per_group": WKE_LAYOUT_PER_GROUP, "shared": WKE_LAYOUT_SHARED,
+                    "separable": WKE_LAYOUT_SEPARABLE}[layout]
         self.d, self.N, self.L = d, N, L
         self.M = n_r * n_s * n_sig
         self.precision = precision

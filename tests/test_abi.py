@@ -141,9 +141,20 @@ def test_shared_field_layout_counts(wke):
     info = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32)
     assert info.shared_fields == 1 and info.products_per_group == 3
     assert info.n_chunks == 32 and info.units_per_collision == 32 * 13
-    assert info.launches_per_collision == 3 + 4 * 32 + 1     # forward: rows, axis 1, axis 0
+    # separable transforms: the 26 shifts are the nonzero points of {-1,0,1}^3 times r/sqrt 3,
+    # so 3 distinct x2 values and 9 distinct (x1, x2) pairs per radius
+    assert info.separable == 1 and info.pair_planes_per_collision == 32 * 9
+    # FP32: the axis-0 transform runs inside the product kernel; per chunk Nyquist
+    # tables, the trailing-axis pass and the fused pass
+    assert info.fused_products == 1
+    assert info.launches_per_collision == 3 + 3 * 32 + 1     # forward: rows, axis 1, axis 0
     fp64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP64)
     assert fp64.units_per_collision == 32 * 13            # a whole radius fits the FP64 budget
+    assert fp64.separable == 1 and fp64.fused_products == 0
+    assert fp64.launches_per_collision == 3 + 4 * 32 + 1
+    unsep = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, layout=wke.WKE_LAYOUT_SHARED)
+    assert unsep.separable == 0 and unsep.fused_products == 1 and unsep.pair_planes_per_collision == 0
+    assert unsep.units_per_collision == 32 * 13
     per_group = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, layout=wke.WKE_LAYOUT_PER_GROUP)
     assert per_group.shared_fields == 0 and per_group.units_per_collision == 256 * 3 + 128
     # with the Nyquist modes zeroed F is not the grid interpolant: no product vanishes
@@ -206,10 +217,24 @@ def test_layout_invariants(wke, d, N, n, sph, sph_sig, prec, nyq):
         assert info.n_groups == n[0] * n[1]
         assert info.n_chunks >= 1 and info.units_per_collision >= 1 and info.device_bytes > 0
         # forward (one kernel per axis), per chunk pass 1 (+ Nyquist tables) and
-        # pass 2, or axis 0 + products in the shared layout, then finalize
-        per_chunk = (3 if nyq == "keep" else 2) + info.shared_fields
+        # pass 2, or axis 0 + products in the shared layout (one fused kernel in
+        # 3D FP32), then finalize
+        per_chunk = (3 if nyq == "keep" else 2) + (info.shared_fields and not info.fused_products)
         assert info.launches_per_collision == d + per_chunk * info.n_chunks + 1
+        # fused only where it applies (3D FP32 shared); it may be declined when
+        # the chunk's fields do not fit the kernel's shared memory
+        assert not info.fused_products or (info.shared_fields and d == 3 and prec == "fp32")
+        assert info.separable == 0 or (info.shared_fields and d == 3)
     assert per_group.shared_fields == 0
+    rc_sep, sep = describe(wke.WKE_LAYOUT_SEPARABLE)
+    if d == 2:
+        assert rc_sep == wke.WKE_ERR_INVALID
+    elif rc_sep == 0:
+        # the same fields and units; the trailing axes once per row value and pair
+        assert sep.separable == 1 and sep.shared_fields == 1
+        assert sep.units_per_collision == shared.units_per_collision
+        assert auto.separable == int(auto.shared_fields == 1 and sep.pair_planes_per_collision
+                                     <= 0.85 * 2 * sep.units_per_collision)
     if rc_shared == 0:
         assert shared.shared_fields == 1
         pick = shared.units_per_collision <= 0.85 * per_group.units_per_collision
