@@ -266,6 +266,13 @@ typedef struct wke_tuning {
     int pass1_units_per_block;     /* units each pass-1 block transforms for its
                                       plane (reuses the plane's coefficients);
                                       0 = automatic */
+    int fuse_products;             /* 3D FP32 shared layouts: 1 = the axis-0
+                                      transform runs inside the product kernel
+                                      (the default where the plan supports
+                                      it), 0 = separate axis-0 and product
+                                      kernels with a unit buffer between them
+                                      (allocated on first use: the call may
+                                      return WKE_ERR_OOM); other plans: 0 */
 } wke_tuning;
 
 int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out);

@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-I" + INCLUDE, "-I" + CSRC]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + CSRC]
 
-CUDA_SOURCES = ["wke_api.cu", "wke_kernels_f32.cu", "wke_kernels_f64.cu", "wke_noalloc.cu", "wke_peak.cu", "wke_server.cu"]
+CUDA_SOURCES = ["wke_api.cu", "wke_kernels_f32.cu", "wke_kernels_f64.cu", "wke_fused64_f32.cu", "wke_fused_f32.cu", "wke_noalloc.cu", "wke_peak.cu", "wke_server.cu"]
 CXX_SOURCES = ["wke_plan.cpp"]
 
 

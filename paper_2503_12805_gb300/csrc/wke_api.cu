@@ -111,6 +111,22 @@ int dev_alloc(wke_plan *p, void **ptr, size_t bytes) {
     return WKE_OK;
 }
 
+// Free the unit buffers (a fused separable plan runs without them).  The
+// caller ensures no queued work uses them.
+void release_unit_buffers(wke_plan *p) {
+    for (void *&h : p->Hbuf) {
+        if (!h) continue;
+        for (size_t i = 0; i < p->allocs.size(); ++i)
+            if (p->allocs[i] == h) {
+                p->allocs.erase(p->allocs.begin() + i);
+                break;
+            }
+        cudaFree(h);
+        p->bytes -= chunk_unit_bytes(p->hp);
+        h = nullptr;
+    }
+}
+
 void free_graphs(wke_plan *p) {
     for (GraphEntry &g : p->graphs) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
@@ -217,6 +233,30 @@ template <typename T> int upload_tables(wke_plan *p) {
     if ((e = cudaMemcpy(const_cast<double *>(p->dp.prod_W), hp.prod_W.data(), hp.prod_W.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "weight upload");
+    if (hp.separable && hp.can_fuse) {
+        // each unit's axis-0 phase rows (fields a, b), interleaved per j1
+        std::vector<float> ue((size_t)total_units(hp) * hp.N * 4, 0.0f);
+        std::vector<double> ra(2 * hp.N), rb(2 * hp.N);
+        for (int c = 0; c < hp.n_chunks; ++c) {
+            const int f0 = hp.chunk_f0[c], K = hp.chunk_f0[c + 1] - f0;
+            for (int u = 0; u < (K + 1) / 2; ++u) {
+                const int fa = f0 + 2 * u;
+                phase_row(hp.N, hp.L, hp.field_shift[(size_t)fa * hp.d], ra.data());
+                const bool pair = 2 * u + 1 < K;
+                if (pair) phase_row(hp.N, hp.L, hp.field_shift[(size_t)(fa + 1) * hp.d], rb.data());
+                float *row = &ue[(size_t)(hp.chunk_u0[c] + u) * hp.N * 4];
+                for (int j = 0; j < hp.N; ++j) {
+                    row[4 * j] = (float)ra[2 * j];
+                    row[4 * j + 1] = (float)ra[2 * j + 1];
+                    row[4 * j + 2] = pair ? (float)rb[2 * j] : 0.0f;
+                    row[4 * j + 3] = pair ? (float)rb[2 * j + 1] : 0.0f;
+                }
+            }
+        }
+        if ((e = cudaMemcpy(const_cast<void *>(p->dp.unit_e0), ue.data(), ue.size() * sizeof(float),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "unit phase upload");
+    }
     if (hp.separable) {
         const std::pair<const std::vector<int> *, const int *> tabs[3] = {
             {&hp.sep_v, p->dp.sep_v}, {&hp.sep_p, p->dp.sep_p}, {&hp.field_pair, p->dp.field_pair}};
@@ -468,6 +508,7 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         ALLOC(p->dp.sep_v, hp.sep_v.size() * sizeof(int));
         ALLOC(p->dp.sep_p, hp.sep_p.size() * sizeof(int));
         ALLOC(p->dp.field_pair, hp.field_pair.size() * sizeof(int));
+        if (hp.can_fuse) ALLOC(p->dp.unit_e0, (size_t)total_units(hp) * hp.N * 16);
     }
     if (hp.nyquist == WKE_NYQ_KEEP) {
         ALLOC(p->Vbuf[0], chunk_v_bytes(hp));
@@ -732,6 +773,7 @@ int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out) {
     if (!plan || !out) return fail(WKE_ERR_INVALID, "plan and out must be non-NULL");
     out->pass2_points_per_thread = effective_p2(plan->hp);
     out->pass1_units_per_block = plan->hp.tune_p1_units_per_block;
+    out->fuse_products = plan->hp.fused ? 1 : 0;
     return WKE_OK;
 }
 
@@ -742,6 +784,22 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
         return fail(WKE_ERR_INVALID, "pass2_points_per_thread must be 4 or 8 (or 12 for N = 3 * 2^a)");
     if (t->pass1_units_per_block < 0 || t->pass1_units_per_block > max_chunk_units(plan->hp))
         return fail(WKE_ERR_INVALID, "pass1_units_per_block must be 0..units per chunk");
+    if (t->fuse_products != 0 && t->fuse_products != 1)
+        return fail(WKE_ERR_INVALID, "fuse_products must be 0 or 1");
+    if (t->fuse_products && !plan->hp.can_fuse)
+        return fail(WKE_ERR_INVALID, "this plan has no fused axis-0 + product kernel (3D FP32 shared layouts only)");
+    if (!t->fuse_products && !plan->Hbuf[0]) {
+        // the separate axis-0 pass needs the unit buffers the fused plan went without
+        plan->hp.fused = false;
+        int rc = dev_alloc(plan, &plan->Hbuf[0], chunk_unit_bytes(plan->hp));
+        if (!rc) rc = dev_alloc(plan, &plan->Hbuf[1], chunk_unit_bytes(plan->hp));
+        if (rc) {
+            plan->hp.fused = true;
+            release_unit_buffers(plan);
+            return rc;
+        }
+    }
+    plan->hp.fused = t->fuse_products == 1;
     plan->hp.tune_p2_points = t->pass2_points_per_thread == 12 ? 8 : t->pass2_points_per_thread;
     plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
     free_graphs(plan);
@@ -756,9 +814,14 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     const int upc = max_chunk_units(hp);
     const int p1s[4] = {0, 1, 2, 3};
     const bool p2_choice = hp.N <= 64 && hp.N % 3 != 0;
-    for (int a = 0; a < (p2_choice ? 2 : 1); ++a)
-        for (int b = 0; b < (hp.d == 3 ? 4 : 1); ++b)
-            if (p1s[b] <= upc) cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b]});
+    // the axis-0 layout matters only where a separate axis-0 pass runs, and
+    // pass 1's units per block only where pass 1 transforms units
+    const bool had_units = plan->Hbuf[0] != nullptr;
+    for (int fz = hp.can_fuse ? 1 : 0; fz >= 0; --fz)
+        for (int a = 0; a < (p2_choice && !fz ? 2 : 1); ++a)
+            for (int b = 0; b < (hp.d == 3 && !hp.separable ? 4 : 1); ++b)
+                if (p1s[b] <= upc)
+                    cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b], fz});
     cudaStream_t s = plan->stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -789,6 +852,11 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     cudaEventDestroy(e1);
     if (rc) return rc;
     if ((rc = wke_plan_set_tuning(plan, &best))) return rc;
+    if (best.fuse_products && !had_units) {   // the unit buffers were only needed while tuning
+        const cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
+        release_unit_buffers(plan);
+    }
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = best_t;
     return WKE_OK;

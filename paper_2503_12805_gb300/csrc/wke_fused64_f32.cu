@@ -1,0 +1,7 @@
+// Single-precision fused axis-0 + product launcher for N = 64 (the staged
+// kernel k_fused64 and its fallback).
+#include "wke_launch.cuh"
+
+namespace wke {
+template WKE_FUSED_AT(float, 64)
+}  // namespace wke

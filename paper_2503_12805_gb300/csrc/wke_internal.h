@@ -89,8 +89,11 @@ struct HostPlan {
     std::vector<int> sep_p;               // per pair: a field with that (x1, x2) (global id)
     std::vector<int> field_pair;          // per field: its pair (chunk-local)
     int max_chunk_pairs = 0, max_chunk_values = 0;
+    std::vector<int> chunk_u0;            // n_chunks + 1: first unit of each chunk (shared layout)
     // The product pass of the shared layout fused with the axis-0 transform
-    // (3D, FP32, not split): no unit buffer between them.
+    // (3D, FP32, not split): no unit buffer between them.  can_fuse is the
+    // capability, fused the current choice (wke_tuning.fuse_products).
+    bool can_fuse = false;
     bool fused = false;
 
     double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)
@@ -144,6 +147,8 @@ struct DevicePtrs {
     const int *sep_v;         // 3 ints per row value (HostPlan::sep_v)
     const int *sep_p;         // per pair: field for the axis-1 phase row
     const int *field_pair;    // per field: chunk-local pair
+    const void *unit_e0;      // FP32 separable: per unit and j1, (E0(j1, x0a), E0(j1, x0b)) as float4
+                              // (zero second part for a lone field)
     const double *prod_W;     // n_groups * products_per_group
 };
 

@@ -1242,6 +1242,216 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
     if (IM) Qim[idx] += (double)sumi + (double)compi;
 }
 
+// 64-point inverse line transform of 4 lines per warp (lane = c + 4 t, thread
+// t of line c holds x[t + 8 e] in v[e] and returns X[t + 8 e]): a radix-8
+// DFT over e in registers, the twiddles w64^{t k1} (wt, per thread), an
+// exchange through `slot` (256 complex entries, the warp's own) and a radix-8
+// DFT over t.  Entry (t, k1) of the exchange sits at k1 * 32 + c + 4 (t ^ k1):
+// the writes of one k1 and the transposed reads of one t both cover 16
+// distinct 8-byte slots per half-warp, so neither has bank conflicts.
+__device__ __forceinline__ void line64_swz(float2 (&v)[8], int c, int t, float2 *__restrict__ slot,
+                                           const float2 (&wt)[8]) {
+    Dft<float, 8, +1>::run(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) v[k] = cmul<float>(v[k], wt[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) slot[k * 32 + c + 4 * (t ^ k)] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = slot[t * 32 + c + 4 * (r ^ t)];
+    __syncwarp();
+    Dft<float, 8, +1>::run(v);
+}
+
+// Fused axis-0 transform and product pass for N = 64 in FP32 with every
+// input staged: the block (4 consecutive columns of one i2 row, 256 points)
+// first copies with cp.async its columns of the chunk's pair planes (or of
+// the pass-1 units) and of the units' Nyquist tables, then each warp
+// transforms whole units from shared memory (the exchange of line64_swz
+// inside the unit's own field slot), and after one barrier every thread forms
+// the products at its point with the algebra and summation order of
+// k_fused_3d.  Shared memory: K field slots, the staged planes, and 324
+// table entries per unit (V_0 at the 4 columns, V_1 at (i1, the 4 i3), V_2
+// at (i1, i2)).  The chunk's product schedule arrives as a kernel parameter
+// with shared-memory byte offsets, so that with the group count a template
+// constant (NGC > 0) every offset and weight is an immediate operand.  When
+// the products of every group share one weight (EQW; the equal-weight rules
+// of Sec. 3.3), a group's sum is formed as
+//   w Re[s P - cf U],  P = sum_p A_p B_p,  U = sum_p (A_p + B_p),
+// the same sum as the per-product form with the weight and the factors s
+// and cf taken out of the product loop.
+constexpr int kF64Pts = 256;
+
+struct Fused64Tab {
+    static constexpr int kMaxProducts = 256, kMaxGroups = 64, kMaxUnits = 128;
+    unsigned oa[kMaxProducts], ob[kMaxProducts];   // byte offsets of each product's fields
+    unsigned oc[kMaxGroups];                       // byte offset of each group's C field
+    float w[kMaxProducts];
+    unsigned char pla[kMaxUnits], plb[kMaxUnits];  // separable plans: pair plane of each unit's fields
+};
+
+template <bool SEP, bool IM, bool NYQ, int PPGC, int NGC, bool EQW>
+__global__ void __launch_bounds__(256, 2)
+k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const float2 *__restrict__ Vtab,
+          const float *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
+          const float2 *__restrict__ tw_g, int K, int ng, int PPG, int nplanes, int ubase,
+          const __grid_constant__ Fused64Tab tab) {
+    constexpr int N = 64, CB = 4, PTS = kF64Pts, P = N * N, VSU = 4 + 64 * 4 + 64;
+    constexpr size_t ND = (size_t)N * P;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *fld = reinterpret_cast<float2 *>(smem_raw);             // K slots of PTS points
+    float2 *pst = fld + (size_t)K * PTS;                              // staged planes: [plane][j1][c]
+    float2 *vst = pst + (size_t)nplanes * PTS;                        // staged tables: [u][VSU]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // two copy groups: the planes (needed by the first transforms), then the
+    // tables (needed after them)
+    const int c = lane & 3, t = lane >> 2;
+    const int col0 = blockIdx.x * CB;
+    const int i2 = col0 >> 6, i30 = col0 & 63;
+    const int U = (K + 1) / 2;
+    // ---- stage the planes: 128 pieces of 16 bytes per plane, two planes per pass
+    {
+        const int j1 = (tid >> 1) & 63, h = tid & 1;
+        const float2 *sp = src + (size_t)j1 * P + col0 + 2 * h;
+        float2 *dp = pst + j1 * CB + 2 * h;
+        for (int pl = tid >> 7; pl < nplanes; pl += 2) cp_async16(dp + (size_t)pl * PTS, sp + (size_t)pl * ND);
+    }
+    cp_async_commit();
+    // ---- stage the tables: per unit, threads 0..127 the V_1 pieces, 128..191
+    // the V_2 entries, 192..193 the V_0 pieces
+    if (NYQ) {
+        if (tid < 128) {
+            const int r = tid >> 1, h = tid & 1;
+            const float2 *sp = Vtab + P + r * N + i30 + 2 * h;
+            float2 *dp = vst + 4 + r * 4 + 2 * h;
+            for (int u = 0; u < U; ++u) cp_async16(dp + (size_t)u * VSU, sp + (size_t)u * 3 * P);
+        } else if (tid < 192) {
+            const int r = tid - 128;
+            const float2 *sp = Vtab + 2 * P + r * N + i2;
+            float2 *dp = vst + 4 + 256 + r;
+            for (int u = 0; u < U; ++u) cp_async_cx<float>(dp + (size_t)u * VSU, sp + (size_t)u * 3 * P);
+        } else if (tid < 194) {
+            const int h = tid - 192;
+            for (int u = 0; u < U; ++u) cp_async16(vst + (size_t)u * VSU + 2 * h, Vtab + (size_t)u * 3 * P + col0 + 2 * h);
+        }
+    }
+    cp_async_commit();
+    float2 wt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wt[k] = tw_g[(t * k) & 63];
+    const float sgn1 = (t & 1) ? -1.0f : 1.0f;                         // (-1)^{i1}
+    const float s2 = (i2 & 1) ? -1.0f : 1.0f, s3 = ((i30 + c) & 1) ? -1.0f : 1.0f;
+    cp_async_wait<1>();
+    __syncthreads();                                                   // planes in place
+    // ---- per unit: axis-0 input and transform, then the unpacking into the
+    // field slots.  Each warp's first unit is transformed while the tables
+    // are still arriving; one block-wide barrier then makes them visible.
+    auto transform = [&](int u, float2 (&v)[8]) {
+        if (SEP) {
+            const float2 *sa = pst + (size_t)tab.pla[u] * PTS + c, *sb = pst + (size_t)tab.plb[u] * PTS + c;
+            const float4 *e0 = ue0 + (size_t)(ubase + u) * N;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j1 = t + 8 * e;
+                const float4 ph = e0[j1];
+                const float2 A = cmul<float>(sa[j1 * CB], make_float2(ph.x, ph.y));
+                const float2 B = cmul<float>(sb[j1 * CB], make_float2(ph.z, ph.w));
+                v[e] = make_float2(A.x - B.y, A.y + B.x);
+            }
+        } else {
+            const float2 *hu = pst + (size_t)u * PTS + c;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = hu[(t + 8 * e) * CB];
+        }
+        line64_swz(v, c, t, fld + (size_t)(2 * u) * PTS, wt);
+    };
+    auto unpack = [&](int u, const float2 (&v)[8]) {
+        const bool pair = 2 * u + 1 < K;
+        float2 *slot = fld + (size_t)(2 * u) * PTS;
+        const float2 *vu = vst + (size_t)u * VSU;
+        const float2 v0 = NYQ ? vu[c] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i1 = t + 8 * e, pt = i1 * CB + c;
+            float a = 0.f, b = 0.f;
+            if (NYQ) {
+                const float2 v1 = vu[4 + i1 * 4 + c], v2 = vu[4 + 256 + i1];
+                a = sgn1 * v0.x + s2 * v1.x + s3 * v2.x;
+                b = sgn1 * v0.y + s2 * v1.y + s3 * v2.y;
+            }
+            slot[pt] = make_float2(v[e].x + b, a);
+            if (pair) slot[PTS + pt] = make_float2(v[e].y - a, b);
+        }
+    };
+    {
+        float2 v[8];
+        if (warp < U) transform(warp, v);
+        cp_async_wait<0>();
+        __syncthreads();                                               // tables in place
+        if (warp < U) unpack(warp, v);
+    }
+    for (int u = warp + 8; u < U; u += 8) {
+        float2 v[8];
+        transform(u, v);
+        unpack(u, v);
+    }
+    __syncthreads();
+    // ---- products at this thread's point
+    const int pt = tid;
+    const size_t idx = (size_t)(pt >> 2) * P + col0 + (pt & 3);
+    const unsigned char *fb = reinterpret_cast<const unsigned char *>(fld + pt);
+    const float F = f[idx];
+    const int ppg = PPGC > 0 ? PPGC : PPG;
+    const int ngr = NGC > 0 ? NGC : ng;
+    float sum = 0.f, comp = 0.f, sumi = 0.f, compi = 0.f;
+#pragma unroll
+    for (int g = 0; g < ngr; ++g) {
+        const float2 C = *reinterpret_cast<const float2 *>(fb + tab.oc[g]);
+        const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
+        float acc = 0.f, acci = 0.f;
+        if (EQW) {
+            // P = sum A B, U = sum (A + B); the group's weight once
+            float2 Pq = make_float2(0.f, 0.f), Uq = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < ppg; ++p) {
+                const int k = g * ppg + p;
+                const float2 A = *reinterpret_cast<const float2 *>(fb + tab.oa[k]);
+                const float2 Bf = *reinterpret_cast<const float2 *>(fb + tab.ob[k]);
+                Pq.x = fmaf(A.x, Bf.x, Pq.x);
+                Pq.x = fmaf(-A.y, Bf.y, Pq.x);
+                Pq.y = fmaf(A.x, Bf.y, Pq.y);
+                Pq.y = fmaf(A.y, Bf.x, Pq.y);
+                Uq = cadd<float>(Uq, cadd<float>(A, Bf));
+            }
+            const float w = tab.w[g * ppg];
+            acc = w * ((sr * Pq.x - si * Pq.y) - (cr * Uq.x - ci * Uq.y));
+            if (IM) acci = w * ((sr * Pq.y + si * Pq.x) - (cr * Uq.y + ci * Uq.x));
+        } else {
+#pragma unroll
+            for (int p = 0; p < ppg; ++p) {
+                const int k = g * ppg + p;
+                const float2 A = *reinterpret_cast<const float2 *>(fb + tab.oa[k]);
+                const float2 Bf = *reinterpret_cast<const float2 *>(fb + tab.ob[k]);
+                const float w = tab.w[k];
+                const float pr = A.x * Bf.x - A.y * Bf.y, pim = A.x * Bf.y + A.y * Bf.x;   // A B
+                const float2 Sab = cadd<float>(A, Bf);                                   // A + B
+                acc += w * ((pr * sr - pim * si) - (cr * Sab.x - ci * Sab.y));
+                if (IM) acci += w * ((pr * si + pim * sr) - (cr * Sab.y + ci * Sab.x));
+            }
+        }
+        float tsum = sum + acc;
+        comp += fabsf(sum) >= fabsf(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+        sum = tsum;
+        if (IM) {
+            tsum = sumi + acci;
+            compi += fabsf(sumi) >= fabsf(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+            sumi = tsum;
+        }
+    }
+    Qacc[idx] += (double)sum + (double)comp;
+    if (IM) Qim[idx] += (double)sumi + (double)compi;
+}
+
 // ------------------------------------------------------------------ finalize
 // Q = scale * sum_g Qacc[g] in group order; the accumulators are cleared.
 template <typename T>

@@ -283,6 +283,51 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
         tab.w[i] = (T)hp.prod_W[slot];
     }
     for (int g = 0; g < cr.ng; ++g) tab.cf[g] = (unsigned char)hp.group_cfield[cr.g0 + g];
+    if constexpr (N == 64 && sizeof(T) == 4) {
+        // every input staged in shared memory, when the chunk's fields, planes
+        // and tables fit
+        const int U = (cr.sK + 1) / 2;
+        const int nplanes = SEP ? hp.chunk_p0[c + 1] - hp.chunk_p0[c] : U;
+        const size_t smem64 = ((size_t)(cr.sK + nplanes) * kF64Pts + (NYQ ? (size_t)U * 324 : 0)) * sizeof(float2);
+        if (smem64 <= kMaxDynamicSmem && U <= Fused64Tab::kMaxUnits) {
+            Fused64Tab t64;
+            for (int i = 0; i < np; ++i) {
+                t64.oa[i] = (unsigned)tab.pa[i] * kF64Pts * sizeof(float2);
+                t64.ob[i] = (unsigned)tab.pb[i] * kF64Pts * sizeof(float2);
+                t64.w[i] = (float)tab.w[i];
+            }
+            for (int g = 0; g < cr.ng; ++g) t64.oc[g] = (unsigned)tab.cf[g] * kF64Pts * sizeof(float2);
+            if (SEP)
+                for (int u = 0; u < U; ++u) {
+                    const int fa = cr.sf0 + 2 * u, fb = 2 * u + 1 < cr.sK ? fa + 1 : fa;
+                    t64.pla[u] = (unsigned char)hp.field_pair[fa];
+                    t64.plb[u] = (unsigned char)hp.field_pair[fb];
+                }
+            const int ubase = hp.chunk_u0[c];
+            int rc = 0;
+#define WKE_F64_LAUNCH(NGC_, EQW_)                                                                              \
+    do {                                                                                                        \
+        if ((rc = set_smem(k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_>, smem64))) return rc;                       \
+        k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_><<<(N * N) / 4, kF64Pts, smem64, s>>>(                          \
+            static_cast<const float2 *>(SEP ? p.S : p.H), static_cast<const float4 *>(p.unit_e0),                 \
+            static_cast<const float2 *>(p.V), static_cast<const float *>(p.f), p.Qacc, p.Qacc_im,                \
+            static_cast<const float2 *>(p.tw), cr.sK, cr.ng, hp.products_per_group, nplanes, ubase, t64);        \
+    } while (0)
+            // one weight per group (every equal-weight sphere rule): the factored product sum
+            bool eqw = PPGC > 0;
+            for (int g = 0; g < cr.ng && eqw; ++g)
+                for (int q = 1; q < PPGC; ++q) eqw = eqw && t64.w[g * PPGC + q] == t64.w[g * PPGC];
+            if constexpr (PPGC == 3 || PPGC == 4) {
+                if (cr.ng == 8 && eqw) WKE_F64_LAUNCH(8, true);
+                else if (cr.ng == 8) WKE_F64_LAUNCH(8, false);
+                else WKE_F64_LAUNCH(0, false);
+            } else {
+                WKE_F64_LAUNCH(0, false);
+            }
+#undef WKE_F64_LAUNCH
+            return (int)cudaGetLastError();
+        }
+    }
     const size_t smem = fused_smem_bytes(N, cr.sK);
     int rc = 0;
     if ((rc = set_smem(k_fused_3d<T, N, SEP, IM, NYQ, PPGC>, smem))) return rc;
@@ -311,8 +356,10 @@ static int fused_ns(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cud
     return im ? fused_nim<T, N, SEP, true, false>(hp, p, c, s) : fused_nim<T, N, SEP, false, false>(hp, p, c, s);
 }
 
+// Instantiated in translation units of their own (wke_fused*.cu), which keeps
+// each compilation short; the other units see them as extern templates.
 template <typename T, int N>
-static int fused_n(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
+int fused_at(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && N <= 64) {
         return hp.separable ? fused_ns<T, N, true>(hp, p, c, im, s) : fused_ns<T, N, false>(hp, p, c, im, s);
     } else {
@@ -514,10 +561,10 @@ template <typename T> int sep_planes_T(const HostPlan &hp, const DevicePtrs &p, 
 
 template <typename T> int fused_T(const HostPlan &hp, const DevicePtrs &p, int c, bool im, cudaStream_t s) {
     switch (hp.N) {
-        case 16: return fused_n<T, 16>(hp, p, c, im, s);
-        case 32: return fused_n<T, 32>(hp, p, c, im, s);
-        case 48: return fused_n<T, 48>(hp, p, c, im, s);
-        case 64: return fused_n<T, 64>(hp, p, c, im, s);
+        case 16: return fused_at<T, 16>(hp, p, c, im, s);
+        case 32: return fused_at<T, 32>(hp, p, c, im, s);
+        case 48: return fused_at<T, 48>(hp, p, c, im, s);
+        case 64: return fused_at<T, 64>(hp, p, c, im, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -618,6 +665,11 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     }
     return rc;
 }
+
+#define WKE_FUSED_AT(T, N) int fused_at<T, N>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
+#define WKE_EXTERN_FUSED(T)                                                                                  \
+    extern template WKE_FUSED_AT(T, 16) extern template WKE_FUSED_AT(T, 32) extern template WKE_FUSED_AT(T, 48) \
+    extern template WKE_FUSED_AT(T, 64)
 
 #define WKE_INSTANTIATE(T)                                                                                   \
     template int dealias_prepare_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                 \

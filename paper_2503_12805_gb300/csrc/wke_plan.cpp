@@ -624,8 +624,13 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
         int maxp = 0;
         for (int c = 0; c < hp.n_chunks; ++c)
             maxp = std::max(maxp, (hp.chunk_g0[c + 1] - hp.chunk_g0[c]) * hp.products_per_group);
-        hp.fused = hp.groups_per_chunk <= kFusedMaxGroups && maxp <= kFusedMaxProducts &&
-                   hp.max_chunk_fields <= 255 && fused_smem_bytes(hp.N, hp.max_chunk_fields) <= 227 * 1024;
+        hp.can_fuse = hp.groups_per_chunk <= kFusedMaxGroups && maxp <= kFusedMaxProducts &&
+                      hp.max_chunk_fields <= 255 && fused_smem_bytes(hp.N, hp.max_chunk_fields) <= 227 * 1024;
+        hp.fused = hp.can_fuse;
+    }
+    if (hp.shared) {
+        hp.chunk_u0.assign(1, 0);
+        for (int c = 0; c < hp.n_chunks; ++c) hp.chunk_u0.push_back(hp.chunk_u0.back() + units_of_chunk(hp, c));
     }
 
     hp.scale = std::ldexp(1.0, 1 - d) * (hp.dispersion == WKE_OMEGA_K2 ? 0.5 : 1.0);
@@ -688,6 +693,7 @@ size_t plan_device_bytes(const HostPlan &hp) {
                                                                         // the forward scratch)
     if (hp.separable)
         bytes += (hp.sep_v.size() + hp.sep_p.size() + hp.field_pair.size()) * sizeof(int);
+    if (hp.separable && hp.can_fuse) bytes += (size_t)total_units(hp) * hp.N * 16;   // unit axis-0 phases
     if (hp.nyquist == WKE_NYQ_KEEP) bytes += 2 * chunk_v_bytes(hp);      // Nyquist tables, double-buffered
     bytes += 2 * (size_t)(hp.shared ? 1 : hp.groups_per_chunk) * nd * 8;   // Qacc, Qacc_im
     bytes += (size_t)hp.n_groups * sizeof(int);                         // C field of each group

@@ -57,7 +57,8 @@ class WkeQuadrature(ctypes.Structure):
 
 
 class WkeTuning(ctypes.Structure):
-    _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int)]
+    _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int),
+                ("fuse_products", ctypes.c_int)]
 
 
 class WkeRequest(ctypes.Structure):
@@ -234,8 +235,12 @@ def wke_plan_get_tuning(plan) -> WkeTuning:
     return t
 
 
-def wke_plan_set_tuning(plan, pass2_points_per_thread: int, pass1_units_per_block: int = 0) -> None:
-    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block)
+def wke_plan_set_tuning(plan, pass2_points_per_thread: int, pass1_units_per_block: int = 0,
+                        fuse_products: int | None = None) -> None:
+    """Set the launch layout; fuse_products None keeps the plan's current choice."""
+    if fuse_products is None:
+        fuse_products = wke_plan_get_tuning(plan).fuse_products
+    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block, fuse_products)
     _check(lib().wke_plan_set_tuning(plan, ctypes.byref(t)))
 
 

@@ -336,20 +336,27 @@ def test_graph_replay_matches_direct_launches():
             assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("layout", ["shared", "separable"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_every_launch_layout_matches_oracle(prec):
-    """Each layout the autotuner may pick computes the same Q (to rounding);
-    the autotuner returns one of them."""
+def test_every_launch_layout_matches_oracle(prec, layout):
+    """Each layout the autotuner may pick computes the same Q (to rounding):
+    axis-0 points per thread, pass-1 units per block and, in FP32, the fused
+    or separate axis-0 and product kernels; the autotuner returns one of
+    them."""
     torch = require_cuda()
     from paper_2503_12805_gb300 import wke
     f = I.gaussian_noise(3, 32, 8.0, 55, 0.1)
     ref, _ = O.collision_fast(f, 8.0, _oracle_quad(3, 8.0, 3, 8, 8, "cube"))
-    with _plan(wke, 3, 32, 8.0, 3, 8, 8, "cube", precision=prec) as plan:
-        for p2 in (4, 8):
-            for p1 in (0, 1, 2, 3):
-                wke.wke_plan_set_tuning(plan.handle, p2, p1)
-                Q = gpu_collision(torch, plan, f)
-                assert rel_max_err(Q, ref) <= TOL[prec], (p2, p1)
+    with _plan(wke, 3, 32, 8.0, 3, 8, 8, "cube", precision=prec, layout=layout) as plan:
+        assert plan.info().separable == (layout == "separable")
+        assert plan.info().fused_products == (prec == "fp32")
+        for fuse in ((1, 0) if prec == "fp32" else (0,)):
+            for p2 in (4, 8):
+                for p1 in (0, 1, 2, 3):
+                    wke.wke_plan_set_tuning(plan.handle, p2, p1, fuse)
+                    assert plan.info().fused_products == fuse
+                    Q = gpu_collision(torch, plan, f)
+                    assert rel_max_err(Q, ref) <= TOL[prec], (fuse, p2, p1)
         ft = torch.tensor(f, dtype=plan.dtype, device="cuda")
         tuning, ms = plan.autotune(ft, reps=2)
         assert tuning.pass2_points_per_thread in (4, 8) and ms > 0
@@ -357,6 +364,9 @@ def test_every_launch_layout_matches_oracle(prec):
         assert rel_max_err(Q, ref) <= TOL[prec]
         with pytest.raises(wke.WkeError):
             wke.wke_plan_set_tuning(plan.handle, 6, 0)
+        if prec == "fp64":
+            with pytest.raises(wke.WkeError):
+                wke.wke_plan_set_tuning(plan.handle, 8, 0, 1)
 
 
 def test_step_graph_matches_direct_launches():

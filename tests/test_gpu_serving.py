@@ -53,7 +53,7 @@ def test_oversize_request_rejected_others_unaffected():
     from paper_2503_12805_gb300 import wke
     small = I.two_gaussians(64, 8.0, 9).astype(np.float32)
     big = I.ring(3, 64, 8.0).astype(np.float32)
-    with wke.Server(device_budget_bytes=64 << 20, max_active=2) as srv:
+    with wke.Server(device_budget_bytes=32 << 20, max_active=2) as srv:
         rid_big, _ = srv.submit(big, 32, 8, 8, 1, 1e-3)
         rid_small, out = srv.submit(small, 16, 4, 4, 2, 1e-3)
         st_big = srv.wait(rid_big, timeout_s=60)
