@@ -1249,11 +1249,12 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
 // DFT over t.  Entry (t, k1) of the exchange sits at k1 * 32 + c + 4 (t ^ k1):
 // the writes of one k1 and the transposed reads of one t both cover 16
 // distinct 8-byte slots per half-warp, so neither has bank conflicts.
+// `tws` is the table exp(2 pi i k / 64), k < 64 (shared memory).
 __device__ __forceinline__ void line64_swz(float2 (&v)[8], int c, int t, float2 *__restrict__ slot,
-                                           const float2 (&wt)[8]) {
+                                           const float2 *__restrict__ tws) {
     Dft<float, 8, +1>::run(v);
 #pragma unroll
-    for (int k = 1; k < 8; ++k) v[k] = cmul<float>(v[k], wt[k]);
+    for (int k = 1; k < 8; ++k) v[k] = cmul<float>(v[k], tws[(t * k) & 63]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) slot[k * 32 + c + 4 * (t ^ k)] = v[k];
     __syncwarp();
@@ -1263,20 +1264,21 @@ __device__ __forceinline__ void line64_swz(float2 (&v)[8], int c, int t, float2 
     Dft<float, 8, +1>::run(v);
 }
 
-// Fused axis-0 transform and product pass for N = 64 in FP32 with every
-// input staged: the block (4 consecutive columns of one i2 row, 256 points)
-// first copies with cp.async its columns of the chunk's pair planes (or of
-// the pass-1 units) and of the units' Nyquist tables, then each warp
-// transforms whole units from shared memory (the exchange of line64_swz
-// inside the unit's own field slot), and after one barrier every thread forms
-// the products at its point with the algebra and summation order of
-// k_fused_3d.  Shared memory: K field slots, the staged planes, and 324
-// table entries per unit (V_0 at the 4 columns, V_1 at (i1, the 4 i3), V_2
-// at (i1, i2)).  The chunk's product schedule arrives as a kernel parameter
-// with shared-memory byte offsets, so that with the group count a template
-// constant (NGC > 0) every offset and weight is an immediate operand.  When
-// the products of every group share one weight (EQW; the equal-weight rules
-// of Sec. 3.3), a group's sum is formed as
+// Fused axis-0 transform and product pass for N = 64 in FP32.  A block holds
+// 4 consecutive columns of one i2 row (256 points, 256 threads) and one field
+// slot of 256 points per field.  It first copies with cp.async its columns of
+// the chunk's pair planes (separable plans) or of the pass-1 units into
+// shared memory, then each warp transforms whole units: the axis-0 input
+// from the staged columns (and, separable, the fields' axis-0 phases), the
+// line transform with the exchange of line64_swz in the unit's first slot,
+// and the unpacking into the unit's two slots with the Nyquist imaginary
+// parts, whose table entries the warp loads from L2 before the transform.
+// After one barrier every thread forms the products at its point with the
+// algebra and summation order of k_fused_3d.  The chunk's product schedule
+// arrives as a kernel parameter with shared-memory byte offsets, so that
+// with the group count a template constant (NGC > 0) every offset and weight
+// is an immediate operand.  When the products of every group share one
+// weight (EQW; the equal-weight rules of Sec. 3.3), a group's sum is formed as
 //   w Re[s P - cf U],  P = sum_p A_p B_p,  U = sum_p (A_p + B_p),
 // the same sum as the per-product form with the weight and the factors s
 // and cf taken out of the product loop.
@@ -1291,20 +1293,18 @@ struct Fused64Tab {
 };
 
 template <bool SEP, bool IM, bool NYQ, int PPGC, int NGC, bool EQW>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const float2 *__restrict__ Vtab,
           const float *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
           const float2 *__restrict__ tw_g, int K, int ng, int PPG, int nplanes, int ubase,
           const __grid_constant__ Fused64Tab tab) {
-    constexpr int N = 64, CB = 4, PTS = kF64Pts, P = N * N, VSU = 4 + 64 * 4 + 64;
+    constexpr int N = 64, CB = 4, PTS = kF64Pts, P = N * N;
     constexpr size_t ND = (size_t)N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *fld = reinterpret_cast<float2 *>(smem_raw);             // K slots of PTS points
     float2 *pst = fld + (size_t)K * PTS;                              // staged planes: [plane][j1][c]
-    float2 *vst = pst + (size_t)nplanes * PTS;                        // staged tables: [u][VSU]
+    float2 *tws = pst + (size_t)nplanes * PTS;                        // twiddles exp(2 pi i k / 64)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // two copy groups: the planes (needed by the first transforms), then the
-    // tables (needed after them)
     const int c = lane & 3, t = lane >> 2;
     const int col0 = blockIdx.x * CB;
     const int i2 = col0 >> 6, i30 = col0 & 63;
@@ -1317,36 +1317,26 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
         for (int pl = tid >> 7; pl < nplanes; pl += 2) cp_async16(dp + (size_t)pl * PTS, sp + (size_t)pl * ND);
     }
     cp_async_commit();
-    // ---- stage the tables: per unit, threads 0..127 the V_1 pieces, 128..191
-    // the V_2 entries, 192..193 the V_0 pieces
-    if (NYQ) {
-        if (tid < 128) {
-            const int r = tid >> 1, h = tid & 1;
-            const float2 *sp = Vtab + P + r * N + i30 + 2 * h;
-            float2 *dp = vst + 4 + r * 4 + 2 * h;
-            for (int u = 0; u < U; ++u) cp_async16(dp + (size_t)u * VSU, sp + (size_t)u * 3 * P);
-        } else if (tid < 192) {
-            const int r = tid - 128;
-            const float2 *sp = Vtab + 2 * P + r * N + i2;
-            float2 *dp = vst + 4 + 256 + r;
-            for (int u = 0; u < U; ++u) cp_async_cx<float>(dp + (size_t)u * VSU, sp + (size_t)u * 3 * P);
-        } else if (tid < 194) {
-            const int h = tid - 192;
-            for (int u = 0; u < U; ++u) cp_async16(vst + (size_t)u * VSU + 2 * h, Vtab + (size_t)u * 3 * P + col0 + 2 * h);
-        }
-    }
-    cp_async_commit();
-    float2 wt[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) wt[k] = tw_g[(t * k) & 63];
+    if (tid < N) tws[tid] = tw_g[tid];
     const float sgn1 = (t & 1) ? -1.0f : 1.0f;                         // (-1)^{i1}
     const float s2 = (i2 & 1) ? -1.0f : 1.0f, s3 = ((i30 + c) & 1) ? -1.0f : 1.0f;
-    cp_async_wait<1>();
-    __syncthreads();                                                   // planes in place
-    // ---- per unit: axis-0 input and transform, then the unpacking into the
-    // field slots.  Each warp's first unit is transformed while the tables
-    // are still arriving; one block-wide barrier then makes them visible.
-    auto transform = [&](int u, float2 (&v)[8]) {
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int u = warp; u < U; u += 8) {
+        const bool pair = 2 * u + 1 < K;
+        // this thread's Nyquist-table entries of unit u (from L2, in flight
+        // during the transform)
+        float2 vr[17];
+        if (NYQ) {
+            const float2 *Vu = Vtab + (size_t)u * 3 * P;
+            vr[16] = Vu[col0 + c];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                vr[e] = Vu[P + (t + 8 * e) * N + i30 + c];
+                vr[8 + e] = Vu[2 * P + (t + 8 * e) * N + i2];
+            }
+        }
+        float2 v[8];
         if (SEP) {
             const float2 *sa = pst + (size_t)tab.pla[u] * PTS + c, *sb = pst + (size_t)tab.plb[u] * PTS + c;
             const float4 *e0 = ue0 + (size_t)(ubase + u) * N;
@@ -1363,37 +1353,20 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = hu[(t + 8 * e) * CB];
         }
-        line64_swz(v, c, t, fld + (size_t)(2 * u) * PTS, wt);
-    };
-    auto unpack = [&](int u, const float2 (&v)[8]) {
-        const bool pair = 2 * u + 1 < K;
         float2 *slot = fld + (size_t)(2 * u) * PTS;
-        const float2 *vu = vst + (size_t)u * VSU;
-        const float2 v0 = NYQ ? vu[c] : make_float2(0.f, 0.f);
+        line64_swz(v, c, t, slot, tws);
+        const float2 v0 = NYQ ? vr[16] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int i1 = t + 8 * e, pt = i1 * CB + c;
+            const int pt = (t + 8 * e) * CB + c;
             float a = 0.f, b = 0.f;
             if (NYQ) {
-                const float2 v1 = vu[4 + i1 * 4 + c], v2 = vu[4 + 256 + i1];
-                a = sgn1 * v0.x + s2 * v1.x + s3 * v2.x;
-                b = sgn1 * v0.y + s2 * v1.y + s3 * v2.y;
+                a = sgn1 * v0.x + s2 * vr[e].x + s3 * vr[8 + e].x;
+                b = sgn1 * v0.y + s2 * vr[e].y + s3 * vr[8 + e].y;
             }
             slot[pt] = make_float2(v[e].x + b, a);
             if (pair) slot[PTS + pt] = make_float2(v[e].y - a, b);
         }
-    };
-    {
-        float2 v[8];
-        if (warp < U) transform(warp, v);
-        cp_async_wait<0>();
-        __syncthreads();                                               // tables in place
-        if (warp < U) unpack(warp, v);
-    }
-    for (int u = warp + 8; u < U; u += 8) {
-        float2 v[8];
-        transform(u, v);
-        unpack(u, v);
     }
     __syncthreads();
     // ---- products at this thread's point

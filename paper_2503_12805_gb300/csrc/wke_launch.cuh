@@ -284,11 +284,10 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
     }
     for (int g = 0; g < cr.ng; ++g) tab.cf[g] = (unsigned char)hp.group_cfield[cr.g0 + g];
     if constexpr (N == 64 && sizeof(T) == 4) {
-        // every input staged in shared memory, when the chunk's fields, planes
-        // and tables fit
+        // field slots, staged planes and twiddles, when they fit
         const int U = (cr.sK + 1) / 2;
         const int nplanes = SEP ? hp.chunk_p0[c + 1] - hp.chunk_p0[c] : U;
-        const size_t smem64 = ((size_t)(cr.sK + nplanes) * kF64Pts + (NYQ ? (size_t)U * 324 : 0)) * sizeof(float2);
+        const size_t smem64 = ((size_t)(cr.sK + nplanes) * kF64Pts + N) * sizeof(float2);
         if (smem64 <= kMaxDynamicSmem && U <= Fused64Tab::kMaxUnits) {
             Fused64Tab t64;
             for (int i = 0; i < np; ++i) {
@@ -304,6 +303,10 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
                     t64.plb[u] = (unsigned char)hp.field_pair[fb];
                 }
             const int ubase = hp.chunk_u0[c];
+            // one weight per group (every equal-weight sphere rule): the factored product sum
+            bool eqw = PPGC > 0;
+            for (int g = 0; g < cr.ng && eqw; ++g)
+                for (int q = 1; q < PPGC; ++q) eqw = eqw && t64.w[g * PPGC + q] == t64.w[g * PPGC];
             int rc = 0;
 #define WKE_F64_LAUNCH(NGC_, EQW_)                                                                              \
     do {                                                                                                        \
@@ -313,10 +316,6 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
             static_cast<const float2 *>(p.V), static_cast<const float *>(p.f), p.Qacc, p.Qacc_im,                \
             static_cast<const float2 *>(p.tw), cr.sK, cr.ng, hp.products_per_group, nplanes, ubase, t64);        \
     } while (0)
-            // one weight per group (every equal-weight sphere rule): the factored product sum
-            bool eqw = PPGC > 0;
-            for (int g = 0; g < cr.ng && eqw; ++g)
-                for (int q = 1; q < PPGC; ++q) eqw = eqw && t64.w[g * PPGC + q] == t64.w[g * PPGC];
             if constexpr (PPGC == 3 || PPGC == 4) {
                 if (cr.ng == 8 && eqw) WKE_F64_LAUNCH(8, true);
                 else if (cr.ng == 8) WKE_F64_LAUNCH(8, false);
