@@ -299,4 +299,26 @@ template <typename T, int N> struct LineCfg {
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
 };
 
+// 64-point inverse line transform of 4 lines per warp (lane = c + 4 t, thread
+// t of line c holds x[t + 8 e] in v[e] and returns X[t + 8 e]): a radix-8
+// DFT over e in registers, the twiddles w64^{t k1} (wt, per thread), an
+// exchange through `slot` (256 complex entries, the warp's own) and a radix-8
+// DFT over t.  Entry (t, k1) of the exchange sits at k1 * 32 + c + 4 (t ^ k1):
+// the writes of one k1 and the transposed reads of one t both cover 16
+// distinct 8-byte slots per half-warp, so neither has bank conflicts.
+// `tws` is the table exp(2 pi i k / 64), k < 64 (shared memory).
+__device__ __forceinline__ void line64_swz(float2 (&v)[8], int c, int t, float2 *__restrict__ slot,
+                                           const float2 *__restrict__ tws) {
+    Dft<float, 8, +1>::run(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) v[k] = cmul<float>(v[k], tws[(t * k) & 63]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) slot[k * 32 + c + 4 * (t ^ k)] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = slot[t * 32 + c + 4 * (r ^ t)];
+    __syncwarp();
+    Dft<float, 8, +1>::run(v);
+}
+
 }  // namespace wke

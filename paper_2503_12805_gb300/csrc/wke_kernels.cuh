@@ -349,6 +349,64 @@ k_sep_planes_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase,
     }
 }
 
+// The same pass for N = 64 in FP32 with warp-local lines only.  Block (j1,
+// row value), 512 threads: each of the 16 warps transforms 4 rows of the
+// plane (lane = row + 4 t holding j3 = t + 8 e) with line64_swz in its own
+// 256-entry slot and writes them to `work`; after one barrier it transforms
+// 4 consecutive columns (lane = column + 4 t holding j2 = t + 8 e) for every
+// pair of the row value and stores them.
+template <int N> struct SepWork64 {
+    static constexpr int WP = N + 4;   // row pitch of `work` (= 4 mod 16: conflict-free column reads per half-warp)
+};
+
+template <int N>
+__global__ void __launch_bounds__(512, 2)
+k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase, float2 *__restrict__ S,
+               const float2 *__restrict__ tw_g, const int *__restrict__ sep_v, const int *__restrict__ sep_p, int v0,
+               int p0) {
+    static_assert(N == 64, "64-point lines");
+    constexpr int WP = SepWork64<N>::WP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tws = reinterpret_cast<float2 *>(smem_raw);            // 64 twiddles
+    float2 *work = tws + N;                                          // N rows of WP
+    float2 *slots = work + N * WP;                                   // 16 warps x 256
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = lane & 3, t = lane >> 2;
+    const int j1 = blockIdx.x, v = v0 + blockIdx.y;
+    const int vf = sep_v[3 * v], pb = sep_v[3 * v + 1], pe = sep_v[3 * v + 2];
+    float2 *slot = slots + (size_t)warp * 256;
+    if (tid < N) tws[tid] = tw_g[tid];
+    const float2 *e2 = phase + (size_t)vf * 3 * N + 2 * N;
+    __syncthreads();
+    {
+        const int j2 = 4 * warp + c;
+        const float2 *grow = ghat + ((size_t)j1 * N + j2) * N;
+        float2 x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = cmul<float>(grow[t + 8 * e], e2[t + 8 * e]);
+        line64_swz(x, c, t, slot, tws);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) work[j2 * WP + t + 8 * e] = x[e];
+    }
+    __syncthreads();
+    const size_t NN = (size_t)N * N;
+    for (int p = pb; p < pe; ++p) {
+        const float2 *e1 = phase + (size_t)sep_p[p0 + p] * 3 * N + N;
+        float2 *out = S + ((size_t)p * N + j1) * NN;
+        {
+            const int i3 = 4 * warp + c;
+            float2 x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = cmul<float>(work[(t + 8 * e) * WP + i3], e1[t + 8 * e]);
+            line64_swz(x, c, t, slot, tws);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) out[(t + 8 * e) * N + i3] = x[e];
+        }
+    }
+}
+
 // 2D: block (row block, unit).  Row j1 of the packed spectrum, inverse
 // transform along axis 1 -> H[unit][j1][y].
 template <typename T, int N>
@@ -1240,28 +1298,6 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
     }
     Qacc[idx] += (double)sum + (double)comp;
     if (IM) Qim[idx] += (double)sumi + (double)compi;
-}
-
-// 64-point inverse line transform of 4 lines per warp (lane = c + 4 t, thread
-// t of line c holds x[t + 8 e] in v[e] and returns X[t + 8 e]): a radix-8
-// DFT over e in registers, the twiddles w64^{t k1} (wt, per thread), an
-// exchange through `slot` (256 complex entries, the warp's own) and a radix-8
-// DFT over t.  Entry (t, k1) of the exchange sits at k1 * 32 + c + 4 (t ^ k1):
-// the writes of one k1 and the transposed reads of one t both cover 16
-// distinct 8-byte slots per half-warp, so neither has bank conflicts.
-// `tws` is the table exp(2 pi i k / 64), k < 64 (shared memory).
-__device__ __forceinline__ void line64_swz(float2 (&v)[8], int c, int t, float2 *__restrict__ slot,
-                                           const float2 *__restrict__ tws) {
-    Dft<float, 8, +1>::run(v);
-#pragma unroll
-    for (int k = 1; k < 8; ++k) v[k] = cmul<float>(v[k], tws[(t * k) & 63]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) slot[k * 32 + c + 4 * (t ^ k)] = v[k];
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = slot[t * 32 + c + 4 * (r ^ t)];
-    __syncwarp();
-    Dft<float, 8, +1>::run(v);
 }
 
 // Fused axis-0 transform and product pass for N = 64 in FP32.  A block holds
