@@ -434,10 +434,10 @@ def run_time_stepping(wke, torch, dev):
     |Q| ~ 770 at max f = 1, so explicit steps of 1e-3 blow up within tens of
     steps; its run uses dt = 1e-5.  Reports steps/s (CUDA events around the
     steps; each step is one graph launch), the relative drift of mass and
-    energy, and the FP32-FP64 difference after the FP64 run's steps."""
+    energy, and the FP32-FP64 difference after the same number of steps."""
     out = {}
     cases = [("2d_n128_m512_rk4", I.WORKLOADS["2d_n128_m512"], 4, 1e-3, 200, 200),
-             ("3d_n64_m2048_rk2", WORKLOAD, 2, 1e-5, 50, 10)]
+             ("3d_n64_m2048_rk2", WORKLOAD, 2, 1e-5, 50, 50)]
     for name, w, stages, dt, steps32, steps64 in cases:
         res, snap = {"dt": dt}, {}
         for prec, steps in (("fp64", steps64), ("fp32", steps32)):
@@ -473,7 +473,8 @@ def run_time_stepping(wke, torch, dev):
 
 # ------------------------------------------------------------------ serving
 
-SERVE_RATE = 200.0      # mean arrivals per second (Poisson)
+SERVE_RATE = 200.0      # mean arrivals per second of the configured stream (Poisson)
+SWEEP_RATES = (20.0, 40.0, 60.0, 80.0)
 
 
 def serving_mix():
@@ -489,14 +490,14 @@ def _serving_initial(d, N, seed):
     return I.ring(3, N, 8.0) if seed % 2 else I.gaussian_noise(3, N, 8.0, seed)
 
 
-def run_serving(n_requests, seed, wke, budget_bytes, max_active):
-    """Poisson stream at SERVE_RATE req/s of mixed requests (1-20 RK4 steps,
-    dt = 1e-3, FP32) through the continuous-batching server; latency is
-    completion minus submission on the server's clock."""
+def run_stream(n_requests, seed, rate, wke, budget_bytes, max_active):
+    """A seeded Poisson stream at `rate` req/s of mixed requests (1-20 RK4
+    steps, dt = 1e-3, FP32) through the continuous-batching server; latency
+    is completion minus submission on the server's clock."""
     import numpy as np
     sizes = serving_mix()
     u = I.splitmix64_uniform(seed, 3 * n_requests)
-    gaps = -np.log(1.0 - u[0::3]) / SERVE_RATE
+    gaps = -np.log(1.0 - u[0::3]) / rate
     arrive = np.cumsum(gaps)
     reqs = []
     for k in range(n_requests):
@@ -505,6 +506,12 @@ def run_serving(n_requests, seed, wke, budget_bytes, max_active):
         reqs.append((d, N, n_r, n_s, n_sig, steps, _serving_initial(d, N, seed + k).astype(np.float32)))
     srv = wke.Server(device_budget_bytes=budget_bytes, max_active=max_active)
     try:
+        # one request of every shape first (not timed), so that plan creation
+        # does not count as latency of the measured stream
+        warm = [srv.submit(r[6], r[2], r[3], r[4], 1, 1e-3)[0] for r in
+                {(r[0], r[1]): r for r in reqs}.values()]
+        for w_id in warm:
+            srv.wait(w_id, timeout_s=600)
         t0 = time.perf_counter()
         ids = []
         for k, (d, N, n_r, n_s, n_sig, steps, f) in enumerate(reqs):
@@ -517,12 +524,26 @@ def run_serving(n_requests, seed, wke, budget_bytes, max_active):
         srv.close()
     ok = [st for st in stats if st.status == wke.WKE_OK]
     lat = np.array([st.t_done - st.t_submit for st in ok]) * 1000.0
+    wait = np.array([st.t_admit - st.t_submit for st in ok]) * 1000.0
     span = max(st.t_done for st in ok) - min(st.t_submit for st in ok)
     evals = sum(4 * r[5] for r in reqs)
-    return {"requests": n_requests, "completed": len(ok), "arrival_rate_req_s": SERVE_RATE,
+    return {"offered_req_s": rate, "requests": n_requests, "completed": len(ok),
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "throughput_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2),
+            "admission_wait_p50_ms": round(float(np.percentile(wait, 50)), 3),
+            "served_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2)}
+
+
+def run_serving(n_requests, seed, wke, budget_bytes, max_active):
+    """Latency and throughput of the mixed stream at offered loads below and
+    at saturation (SWEEP_RATES) and at the configured SERVE_RATE; the served
+    rate at SERVE_RATE is the saturation throughput."""
+    sweep = [run_stream(n_requests, seed + 1000 * i, rate, wke, budget_bytes, max_active)
+             for i, rate in enumerate(SWEEP_RATES)]
+    cfg = run_stream(n_requests, seed, SERVE_RATE, wke, budget_bytes, max_active)
+    return {"sweep": sweep, "configured": cfg, "saturation_req_s": cfg["served_req_s"],
             "max_active": max_active, "budget_gib": round(budget_bytes / 2 ** 30, 1),
+            "latency": "submission to completion on the server clock; one plan of every shape created before "
+                       "each stream",
             "mix": "2D N in {64,128,256} (M=4N), 3D N in {32,48,64} (M=32N); steps U{1..20} RK4, dt=1e-3, FP32"}
 
 
@@ -576,8 +597,8 @@ def main():
     ap.add_argument("--no-rk", dest="rk", action="store_false", help="skip the time-stepping section")
     ap.add_argument("--no-dealias", dest="dealias", action="store_false",
                     help="skip the de-aliased-variant section")
-    ap.add_argument("--serve-requests", type=int, default=120,
-                    help="requests in the serving stream (0: skip serving)")
+    ap.add_argument("--serve-requests", type=int, default=80,
+                    help="requests in each serving stream (0: skip serving)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="only the FP32 timing and kernel split (profiling runs)")
     ap.add_argument("--chunk-mb", type=float, default=0.0,

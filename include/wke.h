@@ -320,10 +320,13 @@ int wke_plan_profile_read(wke_plan *plan, double *out_host);
  * out_dev receives d + 2 doubles; asynchronous on `stream`.
  * The per-block partial sums live in a fixed 40 KiB array in the library's
  * device image, so grids above 4,194,304 points (1024 blocks of 4096) are
- * rejected with WKE_ERR_INVALID.  The first call on each device resolves the
- * array's address with cudaGetSymbolAddress; make that first call before any
- * stream capture.  All calls share the array: calls whose kernels overlap on
- * the GPU race, so order them (one stream, or events). */
+ * rejected with WKE_ERR_INVALID.  A call outside a stream capture resolves
+ * the array's address on the current device with cudaGetSymbolAddress (so
+ * it follows the device image across a cudaDeviceReset); a call inside a
+ * capture uses the address of the last call outside one, so make the first
+ * call on each device before any stream capture.  All calls share the
+ * array: calls whose kernels overlap on the GPU race, so order them (one
+ * stream, or events). */
 int wke_moments_noalloc(int d, int N, double L, int precision, const void *g_dev, double *out_dev,
                         void *stream);
 
@@ -389,6 +392,17 @@ int wke_server_wait(wke_server *server, long long id, double timeout_s, wke_requ
 
 /* Finish every queued request, stop the worker and release all memory. */
 int wke_server_destroy(wke_server *server);
+
+/* Bounds-checked debug build (the library compiled with -DWKE_CHECK,
+ * libwke_check.so): the hot kernels test the indices they take from the
+ * plan's tables against the extents of the buffers they address, record a
+ * bit per failing check site in a device word and skip the access (nothing
+ * traps).  wke_check_status synchronises the device, returns the bits in
+ * *flags, clears them, and returns WKE_ERR_CUDA when any is set (the message
+ * names the sites), WKE_OK otherwise.  In the default build it sets *flags to
+ * 0 and returns WKE_OK.  A debugging aid of the library; the paper has no
+ * counterpart. */
+int wke_check_status(unsigned *flags);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *wke_last_error_string(void);

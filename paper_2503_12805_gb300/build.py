@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libwke.so")
+# the bounds-checked debug build (-DWKE_CHECK)
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(PKG, "libwke_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -49,31 +52,41 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_nvcc=()) -> str:
-    """Compile and link libwke.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def _jobs(build_dir, defines, force, extra_nvcc, nvcc, headers):
+    os.makedirs(build_dir, exist_ok=True)
+    jobs, objs = [], []
+    for src in CUDA_SOURCES:
+        sp = os.path.join(CSRC, src)
+        o = os.path.join(build_dir, src + ".o")
+        objs.append(o)
+        if force or _stale(o, [sp] + headers):
+            jobs.append([nvcc] + ARCH + NVCC_FLAGS + list(defines) + list(extra_nvcc) + ["-c", sp, "-o", o])
+    for src in CXX_SOURCES:
+        sp = os.path.join(CSRC, src)
+        o = os.path.join(build_dir, src + ".o")
+        objs.append(o)
+        if force or _stale(o, [sp] + headers):
+            jobs.append(["g++"] + CXX_FLAGS + list(defines) + ["-c", sp, "-o", o])
+    return jobs, objs
+
+
+def build(verbose: bool = False, force: bool = False, extra_nvcc=(), check: bool = True) -> str:
+    """Compile and link libwke.so (and, with `check`, the bounds-checked
+    libwke_check.so); all translation units compile in parallel.  Returns
+    the path of libwke.so."""
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "wke.h"))
-    jobs, objs = [], []
-    for src in CUDA_SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
-        objs.append(o)
-        if force or _stale(o, [s] + headers):
-            jobs.append([nvcc] + ARCH + NVCC_FLAGS + list(extra_nvcc) + ["-c", s, "-o", o])
-    for src in CXX_SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
-        objs.append(o)
-        if force or _stale(o, [s] + headers):
-            jobs.append(["g++"] + CXX_FLAGS + ["-c", s, "-o", o])
-    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
+    variants = [(BUILD, LIB, ())] + ([(BUILD_CHECK, LIB_CHECK, ("-DWKE_CHECK",))] if check else [])
+    plans = [(lib_path,) + _jobs(d, defs, force, extra_nvcc, nvcc, headers) for d, lib_path, defs in variants]
+    jobs = [j for _, js, _ in plans for j in js]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         for out in ex.map(_run, jobs):
             if verbose and out.strip():
                 print(out)
-    if force or jobs or _stale(LIB, objs):
-        _run([nvcc] + ARCH + ["-shared", "-o", LIB] + objs)
+    for lib_path, js, objs in plans:
+        if force or js or _stale(lib_path, objs):
+            _run([nvcc] + ARCH + ["-shared", "-o", lib_path] + objs)
     return LIB
 
 

@@ -3,12 +3,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
-
+#include "wke_check.cuh"
 #include "wke_internal.h"
+#include "wke_nvtx.h"
 
 namespace wke {
 const char *last_error();
@@ -33,6 +35,30 @@ int moments_partials_count(const HostPlan &) { return 256; }
 
 static int cuda_fail(cudaError_t e, const char *what) {
     return fail(WKE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The bounds-check word of each device (checked builds write it; see
+// wke_check.cuh).  Allocated and zeroed on first use.
+static std::mutex g_check_mutex;
+static unsigned *g_check_word[64] = {nullptr};
+
+unsigned *check_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_check_mutex);
+    if (!g_check_word[dev]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned)) != cudaSuccess || cudaMemset(p, 0, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            if (p) cudaFree(p);
+            return nullptr;
+        }
+        g_check_word[dev] = static_cast<unsigned *>(p);
+    }
+    return g_check_word[dev];
 }
 }  // namespace wke
 
@@ -476,6 +502,7 @@ int wke_plan_footprint_bytes(int d, int N, double L, int M, const wke_quadrature
 }
 
 int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, wke_plan **out) {
+    NvtxRange nvtx_range("wke_plan_create");
     if (!out) return fail(WKE_ERR_INVALID, "out is NULL");
     *out = nullptr;
     wke_plan *p = new (std::nothrow) wke_plan();
@@ -633,16 +660,19 @@ int wke_plan_node_table(const wke_plan *plan, double *out) {
 }
 
 int wke_collision_ex(wke_plan *plan, const void *f, void *Q, void *Qim, void *stream) {
+    NvtxRange nvtx_range("wke_collision_ex");
     if (!plan || !f || !Q) return fail(WKE_ERR_INVALID, "plan, f and Q must be non-NULL");
     if (f == Q || (Qim && (Qim == Q || Qim == f))) return fail(WKE_ERR_INVALID, "f, Q and Qim must not alias");
     return collision(plan, f, Q, Qim, static_cast<cudaStream_t>(stream));
 }
 
 int wke_collision(wke_plan *plan, const void *f, void *Q, void *stream) {
+    NvtxRange nvtx_range("wke_collision");
     return wke_collision_ex(plan, f, Q, nullptr, stream);
 }
 
 int wke_collision_host(wke_plan *plan, const void *f_host, void *Q_host) {
+    NvtxRange nvtx_range("wke_collision_host");
     if (!plan || !f_host || !Q_host) return fail(WKE_ERR_INVALID, "plan, f_host and Q_host must be non-NULL");
     const size_t bytes = grid_in_elems(plan->hp) * (plan->hp.precision == WKE_FP64 ? 8 : 4);
     cudaStream_t s = plan->stream;
@@ -731,6 +761,7 @@ static int step_graph_for(wke_plan *p, void *f, double dt, int stages, cudaGraph
 }
 
 int wke_step(wke_plan *plan, void *f, double dt, int rk_stages) {
+    NvtxRange nvtx_range("wke_step");
     if (!plan || !f) return fail(WKE_ERR_INVALID, "plan and f must be non-NULL");
     if (!std::isfinite(dt)) return fail(WKE_ERR_INVALID, "dt must be finite");
     const double *b, *c;
@@ -894,6 +925,28 @@ int wke_plan_profile_read(wke_plan *plan, double *out) {
 
 const char *wke_last_error_string(void) { return wke::last_error(); }
 
-const char *wke_version(void) { return "wke-gb300 0.1 (sm_103a)"; }
+#ifdef WKE_CHECK
+const char *wke_version(void) { return "wke-gb300 0.2 (sm_103a, bounds-checked)"; }
+#else
+const char *wke_version(void) { return "wke-gb300 0.2 (sm_103a)"; }
+#endif
+
+int wke_check_status(unsigned *flags) {
+    if (!flags) return fail(WKE_ERR_INVALID, "flags is NULL");
+    *flags = 0;
+#ifdef WKE_CHECK
+    unsigned *w = check_word();
+    if (!w) return fail(WKE_ERR_CUDA, "check word unavailable");
+    cudaError_t e = cudaMemcpy(flags, w, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the check word");
+    if (*flags) {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "bounds check failed at sites 0x%x", *flags);
+        return fail(WKE_ERR_CUDA, buf);
+    }
+#endif
+    return WKE_OK;
+}
 
 }  // extern "C"

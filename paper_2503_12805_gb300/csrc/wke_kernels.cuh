@@ -15,6 +15,7 @@
 
 #include <cstdint>
 
+#include "wke_check.cuh"
 #include "wke_fft.cuh"
 #include "wke_internal.h"
 
@@ -363,7 +364,7 @@ template <int N>
 __global__ void __launch_bounds__(512, 2)
 k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase, float2 *__restrict__ S,
                const float2 *__restrict__ tw_g, const int *__restrict__ sep_v, const int *__restrict__ sep_p, int v0,
-               int p0) {
+               int p0, int n_fields, int max_pairs) {
     static_assert(N == 64, "64-point lines");
     constexpr int WP = SepWork64<N>::WP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,6 +375,7 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
     const int c = lane & 3, t = lane >> 2;
     const int j1 = blockIdx.x, v = v0 + blockIdx.y;
     const int vf = sep_v[3 * v], pb = sep_v[3 * v + 1], pe = sep_v[3 * v + 2];
+    if (!WKE_GUARD(vf >= 0 && vf < n_fields && pb >= 0 && pb <= pe && pe <= max_pairs, kChkSepPair)) return;
     float2 *slot = slots + (size_t)warp * 256;
     if (tid < N) tws[tid] = tw_g[tid];
     const float2 *e2 = phase + (size_t)vf * 3 * N + 2 * N;
@@ -392,7 +394,9 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
     __syncthreads();
     const size_t NN = (size_t)N * N;
     for (int p = pb; p < pe; ++p) {
-        const float2 *e1 = phase + (size_t)sep_p[p0 + p] * 3 * N + N;
+        const int pf = sep_p[p0 + p];
+        if (!WKE_GUARD(pf >= 0 && pf < n_fields, kChkSepPair)) continue;
+        const float2 *e1 = phase + (size_t)pf * 3 * N + N;
         float2 *out = S + ((size_t)p * N + j1) * NN;
         {
             const int i3 = 4 * warp + c;
@@ -810,7 +814,7 @@ __device__ __forceinline__ cx<T> sep_input(const cx<T> *__restrict__ sa, const c
 template <typename T, int N, int EP>
 __global__ void __launch_bounds__(Pass2Cfg<T, N, EP>::THREADS)
 k_axis0_sep(const cx<T> *__restrict__ S, const cx<T> *__restrict__ phase, const int *__restrict__ field_pair,
-            cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB, int sf0, int K) {
+            cx<T> *__restrict__ H, const cx<T> *__restrict__ tw_g, int P, int CB, int sf0, int K, int max_pairs) {
     typedef Pass2Cfg<T, N, EP> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -823,7 +827,9 @@ k_axis0_sep(const cx<T> *__restrict__ S, const cx<T> *__restrict__ phase, const 
     const bool pair = 2 * u + 1 < K;
     const int fb = pair ? fa + 1 : fa;
     const size_t ND = (size_t)N * P;
-    const cx<T> *sa = S + (size_t)field_pair[fa] * ND + col, *sb = S + (size_t)field_pair[fb] * ND + col;
+    const int qa = field_pair[fa], qb = field_pair[fb];
+    if (!WKE_GUARD(qa >= 0 && qa < max_pairs && qb >= 0 && qb < max_pairs, kChkAxis0Unit)) return;
+    const cx<T> *sa = S + (size_t)qa * ND + col, *sb = S + (size_t)qb * ND + col;
     const cx<T> *ea = phase + (size_t)fa * 3 * N, *eb = phase + (size_t)fb * 3 * N;
     cx<T> v[E];
 #pragma unroll
@@ -1109,10 +1115,15 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
     cp_async_commit();
     for (int i = threadIdx.x; i < ng * PPG; i += B) {
         const int slot = g0 * PPG + i;
-        ptab[i] = ProdEntry<T>{(unsigned)(prod_local[2 * slot] * B) | ((unsigned)(prod_local[2 * slot + 1] * B) << 16),
-                               (T)prod_W[slot]};
+        int la = prod_local[2 * slot], lb = prod_local[2 * slot + 1];
+        if (!WKE_GUARD(la >= 0 && la < K && lb >= 0 && lb < K, kChkProductsSlot)) la = lb = 0;
+        ptab[i] = ProdEntry<T>{(unsigned)(la * B) | ((unsigned)(lb * B) << 16), (T)prod_W[slot]};
     }
-    for (int i = threadIdx.x; i < ng; i += B) ctab[i] = group_cfield[g0 + i] * B;
+    for (int i = threadIdx.x; i < ng; i += B) {
+        int cf = group_cfield[g0 + i];
+        if (!WKE_GUARD(cf >= 0 && cf < K, kChkProductsSlot)) cf = 0;
+        ctab[i] = cf * B;
+    }
     cp_async_wait<0>();
     __syncthreads();
     const int ppg = PPGC > 0 ? PPGC : PPG;
@@ -1373,6 +1384,8 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
             }
         }
         float2 v[8];
+        if (SEP && !WKE_GUARD(tab.pla[u] < nplanes && tab.plb[u] < nplanes, kChkFusedPlane)) continue;
+        if (!SEP && !WKE_GUARD(u < nplanes, kChkFusedPlane)) continue;
         if (SEP) {
             const float2 *sa = pst + (size_t)tab.pla[u] * PTS + c, *sb = pst + (size_t)tab.plb[u] * PTS + c;
             const float4 *e0 = ue0 + (size_t)(ubase + u) * N;
@@ -1409,13 +1422,16 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
     const int pt = tid;
     const size_t idx = (size_t)(pt >> 2) * P + col0 + (pt & 3);
     const unsigned char *fb = reinterpret_cast<const unsigned char *>(fld + pt);
+    // checked builds: a schedule offset outside the K field slots reads slot 0
+    const unsigned olim = (unsigned)K * PTS * sizeof(float2);
+    auto off = [&](unsigned o) -> unsigned { return WKE_GUARD(o < olim, kChkFusedSchedule) ? o : 0u; };
     const float F = f[idx];
     const int ppg = PPGC > 0 ? PPGC : PPG;
     const int ngr = NGC > 0 ? NGC : ng;
     float sum = 0.f, comp = 0.f, sumi = 0.f, compi = 0.f;
 #pragma unroll
     for (int g = 0; g < ngr; ++g) {
-        const float2 C = *reinterpret_cast<const float2 *>(fb + tab.oc[g]);
+        const float2 C = *reinterpret_cast<const float2 *>(fb + off(tab.oc[g]));
         const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
         float acc = 0.f, acci = 0.f;
         if (EQW) {
@@ -1424,8 +1440,8 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
 #pragma unroll
             for (int p = 0; p < ppg; ++p) {
                 const int k = g * ppg + p;
-                const float2 A = *reinterpret_cast<const float2 *>(fb + tab.oa[k]);
-                const float2 Bf = *reinterpret_cast<const float2 *>(fb + tab.ob[k]);
+                const float2 A = *reinterpret_cast<const float2 *>(fb + off(tab.oa[k]));
+                const float2 Bf = *reinterpret_cast<const float2 *>(fb + off(tab.ob[k]));
                 Pq.x = fmaf(A.x, Bf.x, Pq.x);
                 Pq.x = fmaf(-A.y, Bf.y, Pq.x);
                 Pq.y = fmaf(A.x, Bf.y, Pq.y);
@@ -1439,8 +1455,8 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
 #pragma unroll
             for (int p = 0; p < ppg; ++p) {
                 const int k = g * ppg + p;
-                const float2 A = *reinterpret_cast<const float2 *>(fb + tab.oa[k]);
-                const float2 Bf = *reinterpret_cast<const float2 *>(fb + tab.ob[k]);
+                const float2 A = *reinterpret_cast<const float2 *>(fb + off(tab.oa[k]));
+                const float2 Bf = *reinterpret_cast<const float2 *>(fb + off(tab.ob[k]));
                 const float w = tab.w[k];
                 const float pr = A.x * Bf.x - A.y * Bf.y, pim = A.x * Bf.y + A.y * Bf.x;   // A B
                 const float2 Sab = cadd<float>(A, Bf);                                   // A + B

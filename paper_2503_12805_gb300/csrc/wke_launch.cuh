@@ -9,6 +9,7 @@
 namespace wke {
 
 template <typename K> static int set_smem(K kernel, size_t bytes) {
+    if (int rc = check_bind()) return rc;   // checked builds: this unit's check word (no-op otherwise)
     if (bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return (int)e;
@@ -177,7 +178,8 @@ static int sep_planes_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStre
             if ((rc = set_smem(k_sep_planes64<N>, smem64))) return rc;
             k_sep_planes64<N><<<dim3(N, nv), 512, smem64, s>>>(
                 static_cast<const float2 *>(p.ghat), static_cast<const float2 *>(p.phase), static_cast<float2 *>(p.S),
-                static_cast<const float2 *>(p.tw), p.sep_v, p.sep_p, v0, hp.chunk_p0[c]);
+                static_cast<const float2 *>(p.tw), p.sep_v, p.sep_p, v0, hp.chunk_p0[c], hp.n_fields_total,
+                hp.max_chunk_pairs);
             return (int)cudaGetLastError();
         }
         const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
@@ -249,7 +251,7 @@ static int axis0_sep_ne(const HostPlan &hp, const DevicePtrs &p, int c, cudaStre
     if ((rc = set_smem(k_axis0_sep<T, N, EP>, smem))) return rc;
     k_axis0_sep<T, N, EP><<<dim3(P / CB, cr.units), CB * Cfg::TPL, smem, s>>>(
         static_cast<const cx<T> *>(p.S), static_cast<const cx<T> *>(p.phase), p.field_pair, static_cast<cx<T> *>(p.H),
-        static_cast<const cx<T> *>(p.tw), P, CB, cr.sf0, cr.sK);
+        static_cast<const cx<T> *>(p.tw), P, CB, cr.sf0, cr.sK, hp.max_chunk_pairs);
     return (int)cudaGetLastError();
 }
 

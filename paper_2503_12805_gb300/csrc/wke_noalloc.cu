@@ -81,15 +81,21 @@ __global__ void k_moments_reduce_static(const double *__restrict__ part, int nbl
     }
 }
 
-// Device address of the partial-sum array on the current device, resolved
-// once per device.
-int scratch_address(double **out) {
+// Device address of the partial-sum array on the current device.  Outside a
+// stream capture it is resolved on every call (a device reset reloads the
+// library's device image, which may move the array); inside a capture the
+// address resolved by the last call outside one is used.
+int scratch_address(cudaStream_t s, double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return wke::fail(WKE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return wke::fail(WKE_ERR_UNSUPPORTED, "device ordinal above 63");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess)
+        return wke::fail(WKE_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_addr[dev]) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
         if (e != cudaSuccess || !ptr)
@@ -118,11 +124,11 @@ extern "C" int wke_moments_noalloc(int d, int N, double L, int precision, const 
     if (nd > kMaxPoints)
         return wke::fail(WKE_ERR_INVALID, "grid has more than " + std::to_string(kMaxPoints) +
                                               " points, the most the fixed moment scratch can reduce");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *part = nullptr;
-    int rc = scratch_address(&part);
+    int rc = scratch_address(s, &part);
     if (rc) return rc;
     const int nblocks = (int)((nd + kPointsPerBlock - 1) / kPointsPerBlock);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == WKE_FP64)
         k_moments_partials_static<double><<<nblocks, kThreads, 0, s>>>(static_cast<const double *>(g_dev), d, N, L,
                                                                         nd, part);

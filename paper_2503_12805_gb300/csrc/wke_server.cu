@@ -2,17 +2,23 @@
 //
 // Requests (a grid, a quadrature shape, an RK scheme, a number of steps and
 // a step size) are queued by wke_server_submit from any thread.  One worker
-// thread owns every CUDA call.  It admits the oldest pending request as soon
+// thread owns every CUDA call.  It admits requests in arrival order as soon
 // as a slot is free and the request's device footprint fits the budget
 // (plans of the same shape left by finished requests are reused, and idle
-// plans are evicted least recently used first to make room), copies the
-// initial data through pinned staging, enqueues all steps on the request's
-// own stream, and records a completion event.  Work of different requests
-// therefore overlaps on the device; a request admitted while others run
-// starts immediately.  Completion is detected by polling the events.
+// plans are evicted least recently used first to make room); a request that
+// has to wait for memory may be overtaken by at most kMaxBypass later
+// requests that fit, after which nothing is admitted until it fits.  An
+// admitted request's initial data is copied through pinned staging, all of
+// its steps are enqueued on its own stream and a completion event is
+// recorded, so work of different requests overlaps on the device; a request
+// admitted while others run starts immediately.  Completion is detected by
+// polling the events.  The server mutex guards only the request records
+// (queue, status, times): plan creation, allocation, copies and launches
+// run without it, so submit, cancel and wait never wait behind them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -25,6 +31,7 @@
 #include <vector>
 
 #include "wke_internal.h"
+#include "wke_nvtx.h"
 
 using wke::fail;
 
@@ -52,13 +59,18 @@ struct PlanInst {
 struct Req {
     long long id = 0;
     wke_request r{};
-    int status = 1;                 // 1 pending, 2 active, 0 done, < 0 error
+    int status = 1;                 // 1 pending, 2 active, 0 done, < 0 error (guarded by the mutex)
     double t_submit = 0, t_admit = 0, t_done = 0;
-    PlanInst *inst = nullptr;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    bool cancelled = false;
+    PlanInst *inst = nullptr;       // worker only
+    cudaStream_t stream = nullptr;  // worker only
+    cudaEvent_t done = nullptr;     // worker only
+    bool cancelled = false;         // guarded by the mutex
+    int bypassed = 0;               // worker only: later requests admitted while this one waited
+    size_t need = 0;                // worker only: device bytes of a new plan instance (0: unknown)
 };
+
+// A request waiting for memory is overtaken by at most this many later requests.
+constexpr int kMaxBypass = 8;
 
 size_t grid_bytes_of(const wke_request &r) {
     size_t nd = 1;
@@ -90,12 +102,24 @@ struct wke_server {
     }
 
     // ------------------------------------------------------------ worker side
+    // pool, used, free_streams, active and the worker-only request fields are
+    // touched by the worker thread alone; request status and times are
+    // written under the mutex.
     void free_inst(PlanInst *p) {
         if (p->plan) wke_plan_destroy(p->plan);
         if (p->f_dev) cudaFree(p->f_dev);
         if (p->pin_in) cudaFreeHost(p->pin_in);
         if (p->pin_out) cudaFreeHost(p->pin_out);
         used -= p->dev_bytes;
+    }
+
+    void drop_inst(PlanInst *p) {
+        for (size_t i = 0; i < pool.size(); ++i)
+            if (pool[i].get() == p) {
+                free_inst(p);
+                pool.erase(pool.begin() + i);
+                return;
+            }
     }
 
     bool evict_one_idle() {
@@ -108,37 +132,65 @@ struct wke_server {
         return true;
     }
 
-    // Returns an idle instance for the key, a new one, nullptr when it must
-    // wait for memory, or sets *err when the request can never fit.
-    PlanInst *acquire(const wke_request &r, int *err) {
-        PlanKey key{r.d, r.N, r.n_r, r.n_s, r.n_sig, r.precision, r.rk_stages, r.L};
-        for (auto &p : pool)
-            if (!p->busy && p->key == key) return p.get();
+    static PlanKey key_of(const wke_request &r) {
+        return PlanKey{r.d, r.N, r.n_r, r.n_s, r.n_sig, r.precision, r.rk_stages, r.L};
+    }
+    static wke_quadrature quad_of(const wke_request &r) {
         wke_quadrature q;
         wke_quadrature_default(&q);
         q.n_r = r.n_r;
         q.n_s = r.n_s;
         q.n_sig = r.n_sig;
         q.precision = r.precision;
-        size_t fp = 0;
-        int rc = wke_plan_footprint_bytes(r.d, r.N, r.L, r.n_r * r.n_s * r.n_sig, &q, &fp);
-        if (rc) {
-            *err = rc;
-            return nullptr;
+        return q;
+    }
+    PlanInst *idle_instance(const PlanKey &k) {
+        for (auto &p : pool)
+            if (!p->busy && p->key == k) return p.get();
+        return nullptr;
+    }
+    size_t idle_bytes() const {
+        size_t b = 0;
+        for (const auto &p : pool)
+            if (!p->busy) b += p->dev_bytes;
+        return b;
+    }
+
+    // Whether q can be admitted now (an idle instance of its shape, or room
+    // for a new one once idle instances are evicted); *err is set when it can
+    // never run (invalid shape, or larger than the whole budget).
+    bool fits(Req *q, int *err) {
+        if (idle_instance(key_of(q->r))) return true;
+        if (!q->need) {
+            const wke_quadrature qd = quad_of(q->r);
+            size_t fp = 0;
+            int rc = wke_plan_footprint_bytes(q->r.d, q->r.N, q->r.L, q->r.n_r * q->r.n_s * q->r.n_sig, &qd, &fp);
+            if (rc) {
+                *err = rc;
+                return false;
+            }
+            q->need = fp + grid_bytes_of(q->r);
+            if (q->need > budget) {
+                *err = fail(WKE_ERR_OOM, "request needs " + std::to_string(q->need) + " device bytes, budget is " +
+                                             std::to_string(budget));
+                return false;
+            }
         }
-        const size_t need = fp + grid_bytes_of(r);
-        if (need > budget) {
-            *err = fail(WKE_ERR_OOM, "request needs " + std::to_string(need) + " device bytes, budget is " +
-                                         std::to_string(budget));
-            return nullptr;
+        return used - idle_bytes() + q->need <= budget;
+    }
+
+    // The instance for an admitted request (fits() was true): an idle one of
+    // its shape, or a new one after evicting idle instances.
+    PlanInst *instance_for(Req *q, int *err) {
+        const wke_request &r = q->r;
+        if (PlanInst *p = idle_instance(key_of(r))) return p;
+        while (used + q->need > budget && evict_one_idle()) {
         }
-        while (used + need > budget && evict_one_idle()) {
-        }
-        if (used + need > budget) return nullptr;   // wait for active requests
         auto inst = std::make_unique<PlanInst>();
-        inst->key = key;
+        inst->key = key_of(r);
         inst->grid_bytes = grid_bytes_of(r);
-        rc = wke_plan_create(r.d, r.N, r.L, r.n_r * r.n_s * r.n_sig, &q, &inst->plan);
+        const wke_quadrature qd = quad_of(r);
+        int rc = wke_plan_create(r.d, r.N, r.L, r.n_r * r.n_s * r.n_sig, &qd, &inst->plan);
         if (rc == WKE_OK && cudaMalloc(&inst->f_dev, inst->grid_bytes) != cudaSuccess) rc = WKE_ERR_OOM;
         if (rc == WKE_OK && cudaMallocHost(&inst->pin_in, inst->grid_bytes) != cudaSuccess) rc = WKE_ERR_OOM;
         if (rc == WKE_OK && cudaMallocHost(&inst->pin_out, inst->grid_bytes) != cudaSuccess) rc = WKE_ERR_OOM;
@@ -157,73 +209,130 @@ struct wke_server {
         return pool.back().get();
     }
 
-    void launch(Req *q) {
+    // Copies and all steps of q on its own stream; returns WKE_OK or an error
+    // code, in which case the stream has been drained.
+    int launch(Req *q) {
         PlanInst *p = q->inst;
         const wke_request &r = q->r;
         if (free_streams.empty()) {
             cudaStream_t s;
-            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(WKE_ERR_CUDA, "stream creation failed");
+            }
             free_streams.push_back(s);
         }
         q->stream = free_streams.back();
         free_streams.pop_back();
-        cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming);
-        std::memcpy(p->pin_in, r.f_host, p->grid_bytes);
-        int rc = (int)cudaMemcpyAsync(p->f_dev, p->pin_in, p->grid_bytes, cudaMemcpyHostToDevice, q->stream);
+        int rc = (int)cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming);
+        if (!rc) {
+            std::memcpy(p->pin_in, r.f_host, p->grid_bytes);
+            rc = (int)cudaMemcpyAsync(p->f_dev, p->pin_in, p->grid_bytes, cudaMemcpyHostToDevice, q->stream);
+        }
         if (!rc) rc = wke_plan_set_stream(p->plan, q->stream);
         for (int s = 0; s < r.steps && !rc; ++s) rc = wke_step(p->plan, p->f_dev, r.dt, r.rk_stages);
         if (!rc) rc = (int)cudaMemcpyAsync(p->pin_out, p->f_dev, p->grid_bytes, cudaMemcpyDeviceToHost, q->stream);
         if (!rc) rc = (int)cudaEventRecord(q->done, q->stream);
-        q->status = rc ? (rc > 0 ? WKE_ERR_CUDA : rc) : 2;
+        if (rc) {
+            // work already queued on the stream must end before its buffers are reused
+            cudaStreamSynchronize(q->stream);
+            cudaGetLastError();
+            return rc > 0 ? WKE_ERR_CUDA : rc;
+        }
+        return WKE_OK;
     }
 
+    // Publish q's final status (and its result, status 0); release its
+    // stream and instance.  An instance whose launch failed is destroyed,
+    // since its plan may hold a partial evaluation.
     void finish(Req *q, int status) {
-        q->t_done = now();
         if (status == 0 && q->inst) std::memcpy(q->r.out_host, q->inst->pin_out, q->inst->grid_bytes);
-        q->status = status;
         if (q->inst) {
-            q->inst->busy = false;
-            q->inst->last_used = ++tick;
+            if (status == 0) {
+                q->inst->busy = false;
+                q->inst->last_used = ++tick;
+            } else {
+                drop_inst(q->inst);
+            }
+            q->inst = nullptr;
         }
         if (q->stream) free_streams.push_back(q->stream);
         if (q->done) cudaEventDestroy(q->done);
         q->stream = nullptr;
         q->done = nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        q->t_done = now();
+        q->status = status;
     }
 
     void run() {
         cudaSetDevice(device);
-        std::unique_lock<std::mutex> lk(mu);
+        std::deque<Req *> queue;       // arrival order, not yet admitted
         while (true) {
             bool progress = false;
-            // admissions, oldest first
-            while (!pending.empty() && (int)active.size() < max_active) {
-                Req *q = pending.front();
-                if (q->cancelled) {
-                    pending.pop_front();
-                    q->t_done = now();
-                    q->status = WKE_CANCELLED;
-                    progress = true;
-                    continue;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (queue.empty() && active.empty() && pending.empty()) {
+                    if (stop) break;
+                    cv_work.wait(lk, [&] { return stop || !pending.empty(); });
                 }
+                while (!pending.empty()) {
+                    queue.push_back(pending.front());
+                    pending.pop_front();
+                }
+                for (auto it = queue.begin(); it != queue.end();) {
+                    if ((*it)->cancelled) {
+                        (*it)->t_done = now();
+                        (*it)->status = WKE_CANCELLED;
+                        it = queue.erase(it);
+                        progress = true;
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            if (progress) cv_done.notify_all();
+            // admissions in arrival order; a request waiting for memory is
+            // overtaken by at most kMaxBypass later ones
+            for (size_t i = 0; i < queue.size() && (int)active.size() < max_active;) {
+                Req *q = queue[i];
                 int err = 0;
-                PlanInst *p = acquire(q->r, &err);
-                if (!p && err) {                         // can never run
-                    pending.pop_front();
-                    q->t_done = now();
-                    q->status = err;
+                const bool ok = fits(q, &err);
+                if (err) {                                  // can never run
+                    queue.erase(queue.begin() + i);
+                    finish(q, err);
                     progress = true;
                     continue;
                 }
-                if (!p) break;                           // wait for memory
-                pending.pop_front();
-                p->busy = true;
-                q->inst = p;
-                q->t_admit = now();
-                launch(q);
-                if (q->status != 2) finish(q, q->status);
-                else active.push_back(q);
+                if (!ok) {
+                    if (q->bypassed >= kMaxBypass) break;   // nothing more goes past it
+                    ++i;
+                    continue;
+                }
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (q->cancelled) {
+                        q->t_done = now();
+                        q->status = WKE_CANCELLED;
+                    } else {
+                        q->status = 2;
+                        q->t_admit = now();
+                    }
+                }
+                queue.erase(queue.begin() + i);
                 progress = true;
+                if (q->status == WKE_CANCELLED) continue;
+                wke::NvtxRange nvtx_range("wke_server admission");
+                for (size_t k = 0; k < i; ++k) ++queue[k]->bypassed;
+                q->inst = instance_for(q, &err);
+                if (!q->inst) {
+                    finish(q, err ? err : WKE_ERR_OOM);
+                    continue;
+                }
+                q->inst->busy = true;
+                const int rc = launch(q);
+                if (rc) finish(q, rc);
+                else active.push_back(q);
             }
             // completions
             for (size_t i = 0; i < active.size();) {
@@ -233,15 +342,15 @@ struct wke_server {
                     ++i;
                     continue;
                 }
-                finish(q, e == cudaSuccess ? 0 : WKE_ERR_CUDA);
                 active.erase(active.begin() + i);
+                finish(q, e == cudaSuccess ? 0 : WKE_ERR_CUDA);
                 progress = true;
             }
-            if (progress) cv_done.notify_all();
-            if (stop && pending.empty() && active.empty()) break;
-            if (!progress) {
-                if (active.empty() && pending.empty()) cv_work.wait(lk, [&] { return stop || !pending.empty(); });
-                else cv_work.wait_for(lk, std::chrono::microseconds(50));
+            if (progress) {
+                cv_done.notify_all();
+            } else {
+                std::unique_lock<std::mutex> lk(mu);
+                if (pending.empty()) cv_work.wait_for(lk, std::chrono::microseconds(50));
             }
         }
         for (cudaStream_t s : free_streams) cudaStreamDestroy(s);

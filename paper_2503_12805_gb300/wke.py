@@ -92,9 +92,10 @@ EXPORTED = [
     "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
-    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_alu_peak", "wke_last_error_string",
-    "wke_version",
+    "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_alu_peak", "wke_check_status",
+    "wke_last_error_string", "wke_version",
 ]
+CHECK_LIB_PATH = os.path.join(_HERE, "libwke_check.so")
 PROF_CLASSES = ("forward", "pass1", "pass2", "finalize", "nyquist", "axis0")
 
 
@@ -131,6 +132,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_plan_profile": (i, [vp, i]),
         "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
         "wke_alu_peak": (i, [i, i, C_DOUBLE_P, C_DOUBLE_P]),
+        "wke_check_status": (i, [ctypes.POINTER(ctypes.c_uint)]),
         "wke_last_error_string": (ctypes.c_char_p, []),
         "wke_version": (ctypes.c_char_p, []),
     }
@@ -273,6 +275,30 @@ def wke_alu_peak(precision: int, reps: int = 5):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib().wke_alu_peak(precision, reps, ctypes.byref(tf), ctypes.byref(ms)))
     return tf.value, ms.value
+
+
+def wke_check_status() -> int:
+    """Bounds-check bits of the checked build since the last call (0 in the
+    default build); raises WkeError when any is set."""
+    flags = ctypes.c_uint(0)
+    rc = lib().wke_check_status(ctypes.byref(flags))
+    if rc != WKE_OK and flags.value == 0:
+        _check(rc)
+    return flags.value
+
+
+def use_library(path: str) -> ctypes.CDLL:
+    """Load another build of the library (e.g. CHECK_LIB_PATH) for the calls
+    of this module; returns the previous handle for restore_library."""
+    global _lib
+    prev = _lib if _lib is not None else lib()
+    _lib = load_library(path)
+    return prev
+
+
+def restore_library(handle: ctypes.CDLL) -> None:
+    global _lib
+    _lib = handle
 
 
 def wke_server_create(device_budget_bytes: int, max_active: int):

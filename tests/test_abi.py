@@ -244,3 +244,19 @@ def test_layout_invariants(wke, d, N, n, sph, sph_sig, prec, nyq):
         assert auto.n_chunks == chosen.n_chunks
     else:
         assert auto.shared_fields == 0
+
+
+def test_checked_build_exports_every_symbol(wke):
+    """The bounds-checked debug build (built beside the library) exports the
+    same calls and says so in its version string."""
+    if not os.path.exists(wke.CHECK_LIB_PATH):
+        pytest.skip("checked build not present")
+    lib = ctypes.CDLL(wke.CHECK_LIB_PATH)
+    for name in wke.EXPORTED:
+        assert hasattr(lib, name), name
+    lib.wke_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in lib.wke_version()
+    flags = ctypes.c_uint(7)
+    # without a device the call either reports no failure or a CUDA error; it never aborts
+    rc = lib.wke_check_status(ctypes.byref(flags))
+    assert rc in (0, -3)

@@ -386,26 +386,63 @@ def test_step_graph_matches_direct_launches():
 
 
 def test_workload_2d_n128_rk4_fp32_vs_fp64_and_conservation():
-    """2D N=128, M=512, RK4, dt = 1e-3 (20 of the workload's 200 steps): the
-    FP32 trajectory stays within 1e-5 of the FP64 one, and mass, momentum and
-    energy drift stay small next to their values."""
+    """2D N=128, M=512, RK4, dt = 1e-3, the workload's full 200 steps (Sec. 4
+    integrates with RK4): the FP64 trajectory equals the oracle's rk_step
+    after steps 1 and 2, the FP32 trajectory stays within 1e-5 of the FP64
+    one after 200 steps, and mass and energy drift stay small next to their
+    values."""
     torch = require_cuda()
     from paper_2503_12805_gb300 import wke
     w = I.WORKLOADS["2d_n128_m512"]
     f0 = w.initial()
-    finals, moms = {}, {}
+    quad = _oracle_quad(2, w.L, w.n_r, w.n_s, w.n_sig, w.sphere)
+    oracle_steps = [f0]
+    for _ in range(2):
+        oracle_steps.append(O.rk_step(oracle_steps[-1], w.L, quad, 1e-3, 4))
+    finals, moms, early = {}, {}, {}
     for prec in ("fp64", "fp32"):
         with _plan(wke, 2, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
             ft = torch.tensor(f0, dtype=plan.dtype, device="cuda")
             m0 = plan.moments(ft).cpu().numpy()
-            for _ in range(20):
+            for k in range(200):
                 plan.step(ft, 1e-3, 4)
+                if k < 2:
+                    torch.cuda.synchronize()
+                    early.setdefault(prec, []).append(ft.double().cpu().numpy())
             m1 = plan.moments(ft).cpu().numpy()
             torch.cuda.synchronize()
             finals[prec] = ft.double().cpu().numpy()
             moms[prec] = (m0, m1)
+    for k in range(2):
+        change = np.max(np.abs(oracle_steps[k + 1] - f0))
+        assert np.max(np.abs(early["fp64"][k] - oracle_steps[k + 1])) <= 1e-12 * change, k
     assert rel_max_err(finals["fp32"], finals["fp64"]) <= 1e-5
     m0, m1 = moms["fp64"]
     assert abs(m1[0] - m0[0]) <= 1e-6 * abs(m0[0])       # mass
     assert abs(m1[3] - m0[3]) <= 1e-6 * abs(m0[3])       # energy
+    assert not np.allclose(finals["fp64"], f0)
+
+
+def test_workload_3d_n64_rk2_50_steps_fp32_vs_fp64():
+    """3D N=64, M=2048, ring f, RK2 (Heun) for the workload's 50 steps in both
+    precisions (dt = 1e-5: the ring's |Q| reaches about 770, so explicit
+    steps of 1e-3 are unstable); the FP32 trajectory stays within 1e-5 of the
+    FP64 one at the same step count, and both conserve mass to 1e-6."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    w = I.WORKLOADS["3d_n64_m2048"]
+    f0 = w.initial()
+    finals, mass = {}, {}
+    for prec in ("fp64", "fp32"):
+        with _plan(wke, 3, w.N, w.L, w.n_r, w.n_s, w.n_sig, w.sphere, precision=prec) as plan:
+            ft = torch.tensor(f0, dtype=plan.dtype, device="cuda")
+            m0 = plan.moments(ft).cpu().numpy()
+            for _ in range(50):
+                plan.step(ft, 1e-5, 2)
+            m1 = plan.moments(ft).cpu().numpy()
+            torch.cuda.synchronize()
+            finals[prec] = ft.double().cpu().numpy()
+            mass[prec] = abs(m1[0] - m0[0]) / abs(m0[0])
+    assert rel_max_err(finals["fp32"], finals["fp64"]) <= 1e-5
+    assert mass["fp64"] <= 1e-6 and mass["fp32"] <= 1e-6
     assert not np.allclose(finals["fp64"], f0)
