@@ -273,8 +273,11 @@ def run_gpu(args, rank, world, pool, workers):
         "alu_peaks_measured": {"fp32_tflops": round(peaks32[0], 3), "fp64_tflops": round(peaks64[0], 4),
                                "sms": sms, "clocks": peak_clocks},
         "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
-                   "pass1_units_per_block": tuning.pass1_units_per_block, "autotune_ms": round(tune_ms, 4)},
+                   "pass1_units_per_block": tuning.pass1_units_per_block,
+                   "fuse_products": tuning.fuse_products, "autotune_ms": round(tune_ms, 4)},
         "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
+                 "separable": info.separable, "fused_products": info.fused_products,
+                 "pair_planes_per_eval": info.pair_planes_per_collision, "units_per_eval": info.units_per_collision,
                  "fields_per_group": info.fields_per_group, "products_per_group": info.products_per_group,
                  "flops_per_eval": info.flops_per_collision, "l2_bytes_per_eval": info.l2_bytes_per_collision},
     }
@@ -296,13 +299,16 @@ def run_gpu(args, rank, world, pool, workers):
 
 
 def kernel_flops(cls, info):
-    """Algorithmic flops of one launch of a kernel class (the arithmetic the
-    executed algorithm needs: 5 n log2 n per complex n-point transform, 16 per
-    point for the two phase products and the packing of a unit, 30 per point
-    per product in the fused pass 2; in the product pass of the shared-field
-    layout 12 per unit for the unpacking, 9 per group for s and cf, 17 per
-    product).  A unit is two shifted fields packed in one transform; launch
-    counts are averages over the evaluation's chunks."""
+    """Flops of one launch of a kernel class by the executed algorithm: 5 n
+    log2 n per complex n-point transform; 16 per point for the two phase
+    products and the packing of a unit in pass 1 (separable plans: 6 per
+    point per row value and per pair, and 14 per point per unit for the
+    axis-0 phases and packing); 30 per point per product in the per-group
+    pass 2; in the product pass of the shared-field layout 12 per unit for
+    the unpacking, 9 per group for s and cf, 17 per product.  A unit is two
+    shifted fields packed in one transform; launch counts are averages over
+    the evaluation's chunks.  With fused products the product class also
+    carries the axis-0 transforms."""
     d, N = info.d, info.N_compute
     nd = N ** d
     P = nd // N
@@ -314,13 +320,19 @@ def kernel_flops(cls, info):
         G = info.groups_per_chunk
         units = (G + 1) // 2 + G * ppg
         groups = G
+    axis0 = units * P * 5.0 * N * math.log2(N) + (14.0 * units * nd if info.separable else 0.0)
     if cls == "pass1":
+        if info.separable:
+            # row values along axis 2 and pairs along axis 1 over every plane
+            lines = (info.pair_planes_per_collision + info.row_values_per_collision) / info.n_chunks
+            return lines * nd * (5.0 * math.log2(N) + 6.0)
         return units * N * (5.0 * P * math.log2(P) + 16.0 * P)
     if cls == "axis0":
-        return units * P * 5.0 * N * math.log2(N)
+        return axis0
     if cls == "pass2":
         if info.shared_fields:
-            return nd * (12.0 * units + groups * (9.0 + 17.0 * ppg))
+            prod = nd * (12.0 * units + groups * (9.0 + 17.0 * ppg))
+            return prod + (axis0 if info.fused_products else 0.0)
         per_group = (1 + ppg) * P * 5.0 * N * math.log2(N) + ppg * nd * 30.0
         return groups * per_group
     if cls == "nyquist":   # a chunk's units, two fields per transform

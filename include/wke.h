@@ -168,6 +168,8 @@ typedef struct wke_plan_info {
     int fused_products;      /* 1 when the axis-0 transform and the products
                                 run in one kernel per chunk (3D FP32 shared
                                 layouts)                                       */
+    int row_values_per_collision; /* separable plans: distinct x2 values
+                                transformed along axis 2 per evaluation        */
 } wke_plan_info;
 
 /* ------------------------------------------------------------ calls */

@@ -513,6 +513,16 @@ int wke_plan_create(int d, int N, double L, int M, const wke_quadrature *quad, w
         return rc;
     }
     cudaGetDevice(&p->device);
+    {
+        // checked builds: every kernel unit's check word, before any capture
+        const int brc = check_bind_kernels_f32() | check_bind_kernels_f64() | check_bind_fused64_f32() |
+                        check_bind_fused_f32();
+        if (brc) {
+            cudaGetLastError();
+            delete p;
+            return fail(WKE_ERR_CUDA, "binding the bounds-check word failed");
+        }
+    }
     const HostPlan &hp = p->hp;
     const size_t nd = grid_elems(hp);
     const size_t tb = hp.precision == WKE_FP64 ? 8 : 4, cxb = 2 * tb;
@@ -622,6 +632,7 @@ static void fill_info(const HostPlan &hp, wke_plan_info *info) {
     info->separable = hp.separable ? 1 : 0;
     info->pair_planes_per_collision = hp.separable ? hp.chunk_p0.back() : 0;
     info->fused_products = hp.fused ? 1 : 0;
+    info->row_values_per_collision = hp.separable ? hp.chunk_v0.back() : 0;
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
 }

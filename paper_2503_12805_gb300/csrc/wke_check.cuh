@@ -21,13 +21,20 @@ enum CheckSite : unsigned {
     kChkFusedSchedule = 1u << 1,  // fused kernel: product-schedule offset outside the field slots
     kChkSepPair = 1u << 2,        // separable pass: row value, pair or field id
     kChkProductsSlot = 1u << 3,   // product pass: field slot or table id
-    kChkPass1Field = 1u << 4,     // pass 1: field id of a unit
     kChkAxis0Unit = 1u << 5,      // axis-0 pass: unit or pair id
 };
 
 // Address of the current device's check word (allocated on first use;
 // nullptr if that fails).  Defined in wke_api.cu.
 unsigned *check_word();
+
+// Bind the check word in each kernel translation unit on the current device
+// (checked builds; a no-op returning 0 otherwise).  Called at plan creation,
+// outside any stream capture: the binding copies to constant memory.
+int check_bind_kernels_f32();
+int check_bind_kernels_f64();
+int check_bind_fused64_f32();
+int check_bind_fused_f32();
 
 #ifdef WKE_CHECK
 static __constant__ unsigned *c_wke_check = nullptr;

@@ -4,4 +4,5 @@
 
 namespace wke {
 template WKE_FUSED_AT(float, 64)
+int check_bind_fused64_f32() { return check_bind(); }
 }  // namespace wke

@@ -5,4 +5,5 @@ namespace wke {
 template WKE_FUSED_AT(float, 16)
 template WKE_FUSED_AT(float, 32)
 template WKE_FUSED_AT(float, 48)
+int check_bind_fused_f32() { return check_bind(); }
 }  // namespace wke

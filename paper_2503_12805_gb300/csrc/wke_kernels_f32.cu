@@ -7,4 +7,5 @@
 namespace wke {
 WKE_EXTERN_FUSED(float)
 WKE_INSTANTIATE(float)
+int check_bind_kernels_f32() { return check_bind(); }
 }  // namespace wke

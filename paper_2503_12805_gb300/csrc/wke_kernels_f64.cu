@@ -8,4 +8,5 @@ template WKE_FUSED_AT(double, 32)
 template WKE_FUSED_AT(double, 48)
 template WKE_FUSED_AT(double, 64)
 WKE_INSTANTIATE(double)
+int check_bind_kernels_f64() { return check_bind(); }
 }  // namespace wke

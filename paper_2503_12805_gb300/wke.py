@@ -83,6 +83,7 @@ class WkePlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int), ("shared_fields", ctypes.c_int),
         ("units_per_collision", ctypes.c_int), ("separable", ctypes.c_int),
         ("pair_planes_per_collision", ctypes.c_int), ("fused_products", ctypes.c_int),
+        ("row_values_per_collision", ctypes.c_int),
     ]
 
 
