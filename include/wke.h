@@ -275,6 +275,10 @@ typedef struct wke_tuning {
                                       kernels with a unit buffer between them
                                       (allocated on first use: the call may
                                       return WKE_ERR_OOM); other plans: 0 */
+    int forward_fp32;              /* WKE_FP32 plans that are not de-aliased:
+                                      1 = the forward transform of f computes in
+                                      float, 0 = in double (default); other
+                                      plans: 0 */
 } wke_tuning;
 
 int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out);

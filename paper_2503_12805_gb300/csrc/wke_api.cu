@@ -397,6 +397,11 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         if (!e) e = (int)cudaEventRecord(p->ev_p1[buf], s1);
         if (!e) e = (int)cudaStreamWaitEvent(s2, p->ev_p1[buf], 0);
         if (!e && nyq) e = (int)cudaStreamWaitEvent(s2, p->ev_nq[buf], 0);
+        // a fused plan (not de-aliased) writes Q in its last chunk's product kernel
+        const bool write_q = hp.fused && !hp.dealias && c == hp.n_chunks - 1;
+        dp.Qout = write_q ? Q : nullptr;
+        dp.Qiout = write_q ? Qim : nullptr;
+        dp.scale_out = hp.scale;
         if (!e) {
             ProfScope ps(p, s2, 2);
             e = hp.fused ? fused_T<T>(hp, dp, c, im, s2)
@@ -404,7 +409,7 @@ template <typename T> int enqueue_T(wke_plan *p, const void *f, void *Q, void *Q
         }
         if (!e) e = (int)cudaEventRecord(p->ev_p2[buf], s2);
     }
-    if (!e) {
+    if (!e && !(hp.fused && !hp.dealias)) {
         ProfScope ps(p, s2, 3);
         e = hp.dealias ? dealias_finish_T<T>(hp, dp, Q, Qim, s2) : finalize_T<T>(hp, dp, Q, Qim, s2);
     }
@@ -816,6 +821,7 @@ int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out) {
     out->pass2_points_per_thread = effective_p2(plan->hp);
     out->pass1_units_per_block = plan->hp.tune_p1_units_per_block;
     out->fuse_products = plan->hp.fused ? 1 : 0;
+    out->forward_fp32 = plan->hp.tune_forward_fp32 ? 1 : 0;
     return WKE_OK;
 }
 
@@ -828,6 +834,10 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
         return fail(WKE_ERR_INVALID, "pass1_units_per_block must be 0..units per chunk");
     if (t->fuse_products != 0 && t->fuse_products != 1)
         return fail(WKE_ERR_INVALID, "fuse_products must be 0 or 1");
+    if (t->forward_fp32 != 0 && t->forward_fp32 != 1)
+        return fail(WKE_ERR_INVALID, "forward_fp32 must be 0 or 1");
+    if (t->forward_fp32 && (plan->hp.precision != WKE_FP32 || plan->hp.dealias))
+        return fail(WKE_ERR_INVALID, "forward_fp32 needs a WKE_FP32 plan that is not de-aliased");
     if (t->fuse_products && !plan->hp.can_fuse)
         return fail(WKE_ERR_INVALID, "this plan has no fused axis-0 + product kernel (3D FP32 shared layouts only)");
     if (!t->fuse_products && !plan->Hbuf[0]) {
@@ -842,6 +852,7 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
         }
     }
     plan->hp.fused = t->fuse_products == 1;
+    plan->hp.tune_forward_fp32 = t->forward_fp32 == 1;
     plan->hp.tune_p2_points = t->pass2_points_per_thread == 12 ? 8 : t->pass2_points_per_thread;
     plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
     free_graphs(plan);
@@ -863,7 +874,8 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
         for (int a = 0; a < (p2_choice && !fz ? 2 : 1); ++a)
             for (int b = 0; b < (hp.d == 3 && !hp.separable ? 4 : 1); ++b)
                 if (p1s[b] <= upc)
-                    cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b], fz});
+                    cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b], fz,
+                                               hp.tune_forward_fp32 ? 1 : 0});
     cudaStream_t s = plan->stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

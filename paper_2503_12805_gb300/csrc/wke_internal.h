@@ -101,6 +101,7 @@ struct HostPlan {
     // Launch layout (wke_plan_set_tuning / wke_plan_autotune).
     int tune_p2_points = 8;              // pass-2 points per thread (4 or 8; N >= 128 uses 8)
     int tune_p1_units_per_block = 0;     // pass-1 units per block (0 = automatic: 2 shared, 3 per-group)
+    bool tune_forward_fp32 = false;      // FP32 plans: the forward transform in float (default double)
 };
 
 // Validate arguments and fill `hp` (no device work).  Returns WKE_OK or an
@@ -149,6 +150,10 @@ struct DevicePtrs {
     const int *field_pair;    // per field: chunk-local pair
     const void *unit_e0;      // FP32 separable: per unit and j1, (E0(j1, x0a), E0(j1, x0b)) as float4
                               // (zero second part for a lone field)
+    // fused product kernel, last chunk of an evaluation: write Q (and Im Q)
+    // = scale_out * accumulator and clear the accumulators (null otherwise)
+    void *Qout, *Qiout;
+    double scale_out;
     const double *prod_W;     // n_groups * products_per_group
 };
 

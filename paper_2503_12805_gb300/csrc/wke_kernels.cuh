@@ -73,51 +73,53 @@ __device__ __forceinline__ void twiddle_store(cx<T> *tw, cx<T> mine, const cx<T>
 }
 
 // ------------------------------------------------------------------ forward
-// 3D: forward transform along axis 1 of every (i1, i3) line, in place, in
-// double (the rows were transformed by k_fwd_rows_2d over all N^2 rows).  A
-// warp holds LPW lines of consecutive i3.
-template <int N>
-__global__ void k_fwd_mid_3d(double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
-    typedef LineCfg<double, N> Cfg;
+// The forward transform computes in TC: double (the default) or, on request
+// for FP32 plans, float.
+// 3D: forward transform along axis 1 of every (i1, i3) line, in place (the
+// rows were transformed by k_fwd_rows_2d over all N^2 rows).  A warp holds
+// LPW lines of consecutive i3.
+template <int N, typename TC = double>
+__global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
+    typedef LineCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2 *tw = reinterpret_cast<double2 *>(smem_raw);
-    double2 *scratch = tw + N;
-    load_twiddles<double, N>(tw, tw_g);
+    cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);
+    cx<TC> *scratch = tw + N;
+    load_twiddles<TC, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
     const int line = blockIdx.x * (blockDim.x / 32) * LPW + wl;
     const int i1 = line / N, i3 = line - i1 * N;
-    double2 *base = tmp + (size_t)i1 * N * N + i3;
-    double2 *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
-    double2 v[E];
+    cx<TC> *base = tmp + (size_t)i1 * N * N + i3;
+    cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
+    cx<TC> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = base[(size_t)(t + e * TPL) * N];
-    line_fft<double, N, E, -1>(v, t, scr, tw);
+    line_fft<TC, N, E, -1>(v, t, scr, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) base[(size_t)(t + e * TPL) * N] = v[e];
 }
 
-// Forward transform of every row (the last axis), in double: the N rows of a
-// 2D grid, or the N^2 rows of a 3D one.
-template <typename TIn, int N>
-__global__ void k_fwd_rows_2d(const TIn *__restrict__ f, double2 *__restrict__ tmp, const double2 *__restrict__ tw_g) {
-    typedef LineCfg<double, N> Cfg;
+// Forward transform of every row (the last axis): the N rows of a 2D grid,
+// or the N^2 rows of a 3D one.
+template <typename TIn, int N, typename TC = double>
+__global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
+    typedef LineCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2 *tw = reinterpret_cast<double2 *>(smem_raw);
-    double2 *scratch = tw + N;
-    load_twiddles<double, N>(tw, tw_g);
+    cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);
+    cx<TC> *scratch = tw + N;
+    load_twiddles<TC, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
     const int i1 = blockIdx.x * (blockDim.x / 32) * LPW + wl;
-    double2 *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
-    double2 v[E];
+    cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
+    cx<TC> v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = make_double2((double)f[(size_t)i1 * N + t + e * TPL], 0.0);
-    line_fft<double, N, E, -1>(v, t, scr, tw);
+    for (int e = 0; e < E; ++e) v[e] = mkc<TC>((TC)f[(size_t)i1 * N + t + e * TPL], (TC)0);
+    line_fft<TC, N, E, -1>(v, t, scr, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) tmp[(size_t)i1 * N + t + e * TPL] = v[e];
 }
@@ -128,25 +130,25 @@ __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, double2 *__restrict__ t
 // Nyquist tables: slice ax holds the modes with j_ax = -N/2 (position N/2),
 // indexed by the other axes in increasing order, with the modes that have an
 // earlier axis at -N/2 set to zero (so the slices are disjoint).
-template <typename TOut, int N>
-__global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict__ ghat,
-                           const double2 *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero,
+template <typename TOut, int N, typename TC = double>
+__global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict__ ghat,
+                           const cx<TC> *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero,
                            cx<TOut> *__restrict__ nslice) {
-    typedef LineCfg<double, N> Cfg;
+    typedef LineCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2 *tw = reinterpret_cast<double2 *>(smem_raw);
-    double2 *scratch = tw + N;
-    load_twiddles<double, N>(tw, tw_g);
+    cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);
+    cx<TC> *scratch = tw + N;
+    load_twiddles<TC, N>(tw, tw_g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
     const int col = blockIdx.x * (blockDim.x / 32) * LPW + wl;
-    double2 *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
-    double2 v[E];
+    cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
+    cx<TC> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = tmp[(size_t)(t + e * TPL) * P + col];
-    line_fft<double, N, E, -1>(v, t, scr, tw);
+    line_fft<TC, N, E, -1>(v, t, scr, tw);
     bool col_nyq = false;
     if (nyq_zero) {
         int rest = col;
@@ -158,9 +160,9 @@ __global__ void k_fwd_cols(const double2 *__restrict__ tmp, cx<TOut> *__restrict
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int j1 = t + e * TPL;
-        double2 x = v[e];
-        if (nyq_zero && (col_nyq || j1 == N / 2)) x = make_double2(0.0, 0.0);
-        const cx<TOut> val = mkc<TOut>((TOut)(x.x * inv_nd), (TOut)(x.y * inv_nd));
+        cx<TC> x = v[e];
+        if (nyq_zero && (col_nyq || j1 == N / 2)) x = mkc<TC>((TC)0, (TC)0);
+        const cx<TOut> val = mkc<TOut>((TOut)(x.x * (TC)inv_nd), (TOut)(x.y * (TC)inv_nd));
         ghat[(size_t)j1 * P + col] = val;
         if (nslice) {
             const cx<TOut> zero = mkc<TOut>((TOut)0, (TOut)0);
@@ -1204,6 +1206,27 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
 // its point, the products of all groups of the chunk from the field slots,
 // with the same algebra and summation order as k_products_staged.  The
 // chunk's product table arrives as a kernel parameter.
+// Add a point's chunk total to its FP64 accumulators; in the last chunk of an
+// evaluation (Qout not null) write Q = scale * total instead (and Im Q when
+// Qiout is not null) and clear the accumulators for the next evaluation,
+// which is what the finalize kernel does for the other layouts.
+template <typename T>
+__device__ __forceinline__ void fused_epilogue(double *__restrict__ Qacc, double *__restrict__ Qim, size_t idx,
+                                               double add, double add_im, bool im, T *__restrict__ Qout,
+                                               T *__restrict__ Qiout, double scale) {
+    if (Qout) {
+        Qout[idx] = (T)(scale * (Qacc[idx] + add));
+        Qacc[idx] = 0.0;
+        if (im) {
+            if (Qiout) Qiout[idx] = (T)(scale * (Qim[idx] + add_im));
+            Qim[idx] = 0.0;
+        }
+    } else {
+        Qacc[idx] += add;
+        if (im) Qim[idx] += add_im;
+    }
+}
+
 template <typename T> struct FusedTab {
     static constexpr int kMaxProducts = 256, kMaxGroups = 64;
     unsigned char pa[kMaxProducts], pb[kMaxProducts];   // chunk-local field ids
@@ -1216,7 +1239,7 @@ __global__ void __launch_bounds__(N * LineCfg<T, N>::LPW)
 k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const int *__restrict__ field_pair,
            const cx<T> *__restrict__ Vtab, const T *__restrict__ f, double *__restrict__ Qacc,
            double *__restrict__ Qim, const cx<T> *__restrict__ tw_g, int sf0, int K, int ng, int PPG,
-           const __grid_constant__ FusedTab<T> tab) {
+           const __grid_constant__ FusedTab<T> tab, T *__restrict__ Qout, T *__restrict__ Qiout, double scale) {
     typedef LineCfg<T, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     constexpr int CB = LPW, PTS = N * CB, WARPS = PTS / 32;
@@ -1307,8 +1330,7 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
             sumi = tsum;
         }
     }
-    Qacc[idx] += (double)sum + (double)comp;
-    if (IM) Qim[idx] += (double)sumi + (double)compi;
+    fused_epilogue(Qacc, Qim, idx, (double)sum + (double)comp, (double)sumi + (double)compi, IM, Qout, Qiout, scale);
 }
 
 // Fused axis-0 transform and product pass for N = 64 in FP32.  A block holds
@@ -1344,7 +1366,8 @@ __global__ void __launch_bounds__(256, 3)
 k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const float2 *__restrict__ Vtab,
           const float *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
           const float2 *__restrict__ tw_g, int K, int ng, int PPG, int nplanes, int ubase,
-          const __grid_constant__ Fused64Tab tab) {
+          const __grid_constant__ Fused64Tab tab, float *__restrict__ Qout, float *__restrict__ Qiout,
+          double scale) {
     constexpr int N = 64, CB = 4, PTS = kF64Pts, P = N * N;
     constexpr size_t ND = (size_t)N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1473,8 +1496,7 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
             sumi = tsum;
         }
     }
-    Qacc[idx] += (double)sum + (double)comp;
-    if (IM) Qim[idx] += (double)sumi + (double)compi;
+    fused_epilogue(Qacc, Qim, idx, (double)sum + (double)comp, (double)sumi + (double)compi, IM, Qout, Qiout, scale);
 }
 
 // ------------------------------------------------------------------ finalize

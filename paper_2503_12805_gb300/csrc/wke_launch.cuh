@@ -70,11 +70,14 @@ template <int N> static int spread_warps(int lines) {
 // Forward transform of f on its own grid (N = N_in).  A de-aliased plan
 // writes the coefficients to ghat_in; the padding kernel moves them to the
 // 2N grid.
-template <typename T, int N> static int forward_n(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
-    typedef LineCfg<double, N> Cfg;
+// TC: the compute type of the forward transform (double; float on request
+// for FP32 plans that are not de-aliased, with the plan's float twiddles).
+template <typename T, int N, typename TC>
+static int forward_nc(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
+    typedef LineCfg<TC, N> Cfg;
     const int P = hp.d == 2 ? N : N * N;
-    double2 *tmp = static_cast<double2 *>(p.fwd_tmp);
-    const double2 *tw = reinterpret_cast<const double2 *>(p.tw64);
+    cx<TC> *tmp = static_cast<cx<TC> *>(p.fwd_tmp);
+    const cx<TC> *tw = sizeof(TC) == 8 ? reinterpret_cast<const cx<TC> *>(p.tw64) : static_cast<const cx<TC> *>(p.tw);
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
@@ -82,28 +85,36 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
             // kernels over the whole grid, so every SM takes part in the FP64 work
             const int rows = N * N;
             const int warps = spread_warps<N>(rows);
-            const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
-            if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
-            k_fwd_rows_2d<T, N><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
-            if ((rc = set_smem(k_fwd_mid_3d<N>, smem))) return rc;
-            k_fwd_mid_3d<N><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
+            const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
+            k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f),
+                                                                                       tmp, tw);
+            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, smem))) return rc;
+            k_fwd_mid_3d<N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
         } else {
             return (int)cudaErrorInvalidValue;
         }
     } else {
         const int warps = spread_warps<N>(N);
-        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
-        if ((rc = set_smem(k_fwd_rows_2d<T, N>, smem))) return rc;
-        k_fwd_rows_2d<T, N><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
+        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+        if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
+        k_fwd_rows_2d<T, N, TC><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f), tmp, tw);
     }
     const int warps = spread_warps<N>(P);
-    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(double2);
-    if ((rc = set_smem(k_fwd_cols<T, N>, smem))) return rc;
+    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+    if ((rc = set_smem(k_fwd_cols<T, N, TC>, smem))) return rc;
     const double inv_nd = 1.0 / (double)nd_in(hp);
-    k_fwd_cols<T, N><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(
+    k_fwd_cols<T, N, TC><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(
         tmp, static_cast<cx<T> *>(hp.dealias ? p.ghat_in : p.ghat), tw, P, hp.d, inv_nd, hp.nyquist == WKE_NYQ_ZERO,
         hp.nyquist == WKE_NYQ_KEEP ? static_cast<cx<T> *>(p.nslice) : nullptr);
     return (int)cudaGetLastError();
+}
+
+template <typename T, int N> static int forward_n(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (hp.tune_forward_fp32 && !hp.dealias) return forward_nc<T, N, float>(hp, p, s);
+    }
+    return forward_nc<T, N, double>(hp, p, s);
 }
 
 // ------------------------------------------------------------------ pass 1
@@ -324,7 +335,8 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
         k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_><<<(N * N) / 4, kF64Pts, smem64, s>>>(                          \
             static_cast<const float2 *>(SEP ? p.S : p.H), static_cast<const float4 *>(p.unit_e0),                 \
             static_cast<const float2 *>(p.V), static_cast<const float *>(p.f), p.Qacc, p.Qacc_im,                \
-            static_cast<const float2 *>(p.tw), cr.sK, cr.ng, hp.products_per_group, nplanes, ubase, t64);        \
+            static_cast<const float2 *>(p.tw), cr.sK, cr.ng, hp.products_per_group, nplanes, ubase, t64,          \
+            static_cast<float *>(p.Qout), static_cast<float *>(p.Qiout), p.scale_out);                          \
     } while (0)
             if constexpr (PPGC == 3 || PPGC == 4) {
                 if (cr.ng == 8 && eqw) WKE_F64_LAUNCH(8, true);
@@ -343,7 +355,8 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
     k_fused_3d<T, N, SEP, IM, NYQ, PPGC><<<(N * N) / CB, PTS, smem, s>>>(
         static_cast<const cx<T> *>(SEP ? p.S : p.H), static_cast<const cx<T> *>(p.phase), p.field_pair,
         static_cast<const cx<T> *>(p.V), static_cast<const T *>(p.f), p.Qacc, p.Qacc_im,
-        static_cast<const cx<T> *>(p.tw), cr.sf0, cr.sK, cr.ng, hp.products_per_group, tab);
+        static_cast<const cx<T> *>(p.tw), cr.sf0, cr.sK, cr.ng, hp.products_per_group, tab, static_cast<T *>(p.Qout),
+        static_cast<T *>(p.Qiout), p.scale_out);
     return (int)cudaGetLastError();
 }
 

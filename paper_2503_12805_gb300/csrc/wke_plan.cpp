@@ -667,10 +667,11 @@ size_t chunk_s_bytes(const HostPlan &hp) {
 // per chunk the Nyquist tables (Nyquist kept), the trailing-axis pass, the
 // axis-0 transform (shared layout, unless fused with the products) and the
 // product pass, then finalize (de-aliased plans: 1 padding + d maps before,
-// 1 + d maps after instead of finalize).
+// 1 + d maps after instead of finalize; fused plans write Q in the last
+// chunk's product kernel instead).
 int launches_per_collision(const HostPlan &hp) {
     int per_chunk = (hp.nyquist == WKE_NYQ_KEEP ? 1 : 0) + 2 + (hp.shared && !hp.fused ? 1 : 0);
-    int n = hp.d + per_chunk * hp.n_chunks + 1;
+    int n = hp.d + per_chunk * hp.n_chunks + (hp.fused && !hp.dealias ? 0 : 1);
     if (hp.dealias) n += 1 + hp.d + hp.d;
     return n;
 }

@@ -58,7 +58,7 @@ class WkeQuadrature(ctypes.Structure):
 
 class WkeTuning(ctypes.Structure):
     _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int),
-                ("fuse_products", ctypes.c_int)]
+                ("fuse_products", ctypes.c_int), ("forward_fp32", ctypes.c_int)]
 
 
 class WkeRequest(ctypes.Structure):
@@ -239,11 +239,14 @@ def wke_plan_get_tuning(plan) -> WkeTuning:
 
 
 def wke_plan_set_tuning(plan, pass2_points_per_thread: int, pass1_units_per_block: int = 0,
-                        fuse_products: int | None = None) -> None:
-    """Set the launch layout; fuse_products None keeps the plan's current choice."""
+                        fuse_products: int | None = None, forward_fp32: int | None = None) -> None:
+    """Set the launch layout; fuse_products / forward_fp32 None keep the plan's current choice."""
+    cur = wke_plan_get_tuning(plan)
     if fuse_products is None:
-        fuse_products = wke_plan_get_tuning(plan).fuse_products
-    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block, fuse_products)
+        fuse_products = cur.fuse_products
+    if forward_fp32 is None:
+        forward_fp32 = cur.forward_fp32
+    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block, fuse_products, forward_fp32)
     _check(lib().wke_plan_set_tuning(plan, ctypes.byref(t)))
 
 

@@ -147,7 +147,8 @@ def test_shared_field_layout_counts(wke):
     # FP32: the axis-0 transform runs inside the product kernel; per chunk Nyquist
     # tables, the trailing-axis pass and the fused pass
     assert info.fused_products == 1
-    assert info.launches_per_collision == 3 + 3 * 32 + 1     # forward: rows, axis 1, axis 0
+    # (no finalize launch: the last chunk's product kernel writes Q)
+    assert info.launches_per_collision == 3 + 3 * 32         # forward: rows, axis 1, axis 0
     fp64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP64)
     assert fp64.units_per_collision == 32 * 13            # a whole radius fits the FP64 budget
     assert fp64.separable == 1 and fp64.fused_products == 0
@@ -220,7 +221,8 @@ def test_layout_invariants(wke, d, N, n, sph, sph_sig, prec, nyq):
         # pass 2, or axis 0 + products in the shared layout (one fused kernel in
         # 3D FP32), then finalize
         per_chunk = (3 if nyq == "keep" else 2) + (info.shared_fields and not info.fused_products)
-        assert info.launches_per_collision == d + per_chunk * info.n_chunks + 1
+        finalize = 0 if info.fused_products else 1
+        assert info.launches_per_collision == d + per_chunk * info.n_chunks + finalize
         # fused only where it applies (3D FP32 shared); it may be declined when
         # the chunk's fields do not fit the kernel's shared memory
         assert not info.fused_products or (info.shared_fields and d == 3 and prec == "fp32")

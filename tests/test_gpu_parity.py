@@ -350,13 +350,15 @@ def test_every_launch_layout_matches_oracle(prec, layout):
     with _plan(wke, 3, 32, 8.0, 3, 8, 8, "cube", precision=prec, layout=layout) as plan:
         assert plan.info().separable == (layout == "separable")
         assert plan.info().fused_products == (prec == "fp32")
-        for fuse in ((1, 0) if prec == "fp32" else (0,)):
-            for p2 in (4, 8):
-                for p1 in (0, 1, 2, 3):
-                    wke.wke_plan_set_tuning(plan.handle, p2, p1, fuse)
-                    assert plan.info().fused_products == fuse
-                    Q = gpu_collision(torch, plan, f)
-                    assert rel_max_err(Q, ref) <= TOL[prec], (fuse, p2, p1)
+        for fwd32 in ((0, 1) if prec == "fp32" else (0,)):
+            for fuse in ((1, 0) if prec == "fp32" else (0,)):
+                for p2 in (4, 8):
+                    for p1 in (0, 1, 2, 3):
+                        wke.wke_plan_set_tuning(plan.handle, p2, p1, fuse, fwd32)
+                        assert plan.info().fused_products == fuse
+                        Q = gpu_collision(torch, plan, f)
+                        assert rel_max_err(Q, ref) <= TOL[prec], (fwd32, fuse, p2, p1)
+        wke.wke_plan_set_tuning(plan.handle, 8, 0, int(prec == "fp32"), 0)
         ft = torch.tensor(f, dtype=plan.dtype, device="cuda")
         tuning, ms = plan.autotune(ft, reps=2)
         assert tuning.pass2_points_per_thread in (4, 8) and ms > 0
@@ -367,6 +369,8 @@ def test_every_launch_layout_matches_oracle(prec, layout):
         if prec == "fp64":
             with pytest.raises(wke.WkeError):
                 wke.wke_plan_set_tuning(plan.handle, 8, 0, 1)
+            with pytest.raises(wke.WkeError):
+                wke.wke_plan_set_tuning(plan.handle, 8, 0, 0, 1)
 
 
 def test_step_graph_matches_direct_launches():
