@@ -342,7 +342,7 @@ def kernel_flops(cls, info):
     return 2.0 * groups * nd
 
 
-def survey_flops(cls, info):
+def paper_flops(cls, info):
     """Flops of one launch of a kernel class by the per-node count of the
     paper's algorithm (Sec. 3.4 complexity paragraph): per node 2 + 1/N_sig
     inverse transforms of N^d points at 5 N^d log2 N^d flops, 6 d N^d for the
@@ -385,13 +385,13 @@ def roofline_of(prof, info, peak32):
     per_launch_s = dom_ms / dom_n * 1e-3
     peak = peak32[0]
     achieved = kernel_flops(dom, info) / per_launch_s / 1e12
-    paper = survey_flops(dom, info) / per_launch_s / 1e12
+    paper = paper_flops(dom, info) / per_launch_s / 1e12
     traffic = DRAM_BYTES_3D_N64.get(dom) if (info.d, info.N_compute, info.precision) == (3, 64, 1) else None
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": "wke_alu_peak(WKE_FP32): FMA chains on every SM, measured in this run (of measured)",
             "flops_per_launch": kernel_flops(dom, info),
-            "paper_algorithm_flops_per_launch": survey_flops(dom, info),
+            "paper_algorithm_flops_per_launch": paper_flops(dom, info),
             "paper_algorithm_achieved": round(paper, 3), "paper_algorithm_frac": round(paper / peak, 4),
             "per_launch_ms": round(dom_ms / dom_n, 5), "launches": dom_n,
             "kernel_share": {c: round(v[0] / total, 4) for c, v in classes.items()},
