@@ -274,7 +274,8 @@ def run_gpu(args, rank, world, pool, workers):
                                "sms": sms, "clocks": peak_clocks},
         "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
                    "pass1_units_per_block": tuning.pass1_units_per_block,
-                   "fuse_products": tuning.fuse_products, "autotune_ms": round(tune_ms, 4)},
+                   "fuse_products": tuning.fuse_products, "rule_products": tuning.rule_products,
+                   "autotune_ms": round(tune_ms, 4)},
         "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
                  "separable": info.separable, "fused_products": info.fused_products,
                  "pair_planes_per_eval": info.pair_planes_per_collision, "units_per_eval": info.units_per_collision,

@@ -170,6 +170,8 @@ typedef struct wke_plan_info {
                                 layouts)                                       */
     int row_values_per_collision; /* separable plans: distinct x2 values
                                 transformed along axis 2 per evaluation        */
+    int rule_products_available; /* 1 when the plan has the cube rule's own
+                                product schedule (wke_tuning.rule_products)    */
 } wke_plan_info;
 
 /* ------------------------------------------------------------ calls */
@@ -279,6 +281,12 @@ typedef struct wke_tuning {
                                       1 = the forward transform of f computes in
                                       float, 0 = in double (default); other
                                       plans: 0 */
+    int rule_products;             /* fused plans of the cube rule (cube q-hat
+                                      and sigma rules, antipodal pairing): 1 =
+                                      the products follow the rule's own
+                                      schedule, which reads every field once
+                                      per point (the default), 0 = the generic
+                                      product table; other plans: 0 */
 } wke_tuning;
 
 int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out);

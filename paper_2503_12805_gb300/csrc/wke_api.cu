@@ -638,6 +638,7 @@ static void fill_info(const HostPlan &hp, wke_plan_info *info) {
     info->pair_planes_per_collision = hp.separable ? hp.chunk_p0.back() : 0;
     info->fused_products = hp.fused ? 1 : 0;
     info->row_values_per_collision = hp.separable ? hp.chunk_v0.back() : 0;
+    info->rule_products_available = hp.cube.empty() ? 0 : 1;
     info->flops_per_collision = plan_flops(hp);
     info->l2_bytes_per_collision = plan_l2_bytes(hp);
 }
@@ -822,6 +823,7 @@ int wke_plan_get_tuning(const wke_plan *plan, wke_tuning *out) {
     out->pass1_units_per_block = plan->hp.tune_p1_units_per_block;
     out->fuse_products = plan->hp.fused ? 1 : 0;
     out->forward_fp32 = plan->hp.tune_forward_fp32 ? 1 : 0;
+    out->rule_products = plan->hp.fused && !plan->hp.cube.empty() && plan->hp.tune_rule_products ? 1 : 0;
     return WKE_OK;
 }
 
@@ -838,6 +840,10 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
         return fail(WKE_ERR_INVALID, "forward_fp32 must be 0 or 1");
     if (t->forward_fp32 && (plan->hp.precision != WKE_FP32 || plan->hp.dealias))
         return fail(WKE_ERR_INVALID, "forward_fp32 needs a WKE_FP32 plan that is not de-aliased");
+    if (t->rule_products != 0 && t->rule_products != 1)
+        return fail(WKE_ERR_INVALID, "rule_products must be 0 or 1");
+    if (t->rule_products && (!t->fuse_products || plan->hp.cube.empty()))
+        return fail(WKE_ERR_INVALID, "rule_products needs fuse_products and a plan of the cube rule");
     if (t->fuse_products && !plan->hp.can_fuse)
         return fail(WKE_ERR_INVALID, "this plan has no fused axis-0 + product kernel (3D FP32 shared layouts only)");
     if (!t->fuse_products && !plan->Hbuf[0]) {
@@ -853,6 +859,7 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *t) {
     }
     plan->hp.fused = t->fuse_products == 1;
     plan->hp.tune_forward_fp32 = t->forward_fp32 == 1;
+    if (t->fuse_products) plan->hp.tune_rule_products = t->rule_products == 1;
     plan->hp.tune_p2_points = t->pass2_points_per_thread == 12 ? 8 : t->pass2_points_per_thread;
     plan->hp.tune_p1_units_per_block = t->pass1_units_per_block;
     free_graphs(plan);
@@ -873,9 +880,10 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     for (int fz = hp.can_fuse ? 1 : 0; fz >= 0; --fz)
         for (int a = 0; a < (p2_choice && !fz ? 2 : 1); ++a)
             for (int b = 0; b < (hp.d == 3 && !hp.separable ? 4 : 1); ++b)
-                if (p1s[b] <= upc)
-                    cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b], fz,
-                                               hp.tune_forward_fp32 ? 1 : 0});
+                for (int rp = fz && !hp.cube.empty() ? 1 : 0; rp >= 0; --rp)
+                    if (p1s[b] <= upc)
+                        cands.push_back(wke_tuning{p2_choice ? p2s[a] : effective_p2(hp), p1s[b], fz,
+                                                   hp.tune_forward_fp32 ? 1 : 0, rp});
     cudaStream_t s = plan->stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

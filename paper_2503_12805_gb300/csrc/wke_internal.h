@@ -94,6 +94,22 @@ struct HostPlan {
     // (3D, FP32, not split): no unit buffer between them.  can_fuse is the
     // capability, fused the current choice (wke_tuning.fuse_products).
     bool can_fuse = false;
+    // The cube rule's own product schedule for the fused kernel (3D N = 64,
+    // shared layout, cube q-hat and sigma rules with antipodal pairing): in every
+    // chunk the fields are the 26 shifts m s, s in {-1, 0, 1}^3 \ {0}; group
+    // v (a vertex, s = v, its C field) has the three products (edge field of
+    // axis i with sign v_i, face field with component i zero and the other
+    // signs of v), i = 0, 1, 2.  Per chunk, chunk-local field ids of the edge
+    // fields (index 2 i + [sign < 0]), the face fields (index 4 i + q, bit 0 of
+    // q: the lower other axis negative, bit 1: the higher one) and the C
+    // fields, and the group weights, both by vertex (bit a: v_a < 0).  Empty
+    // unless every chunk has this form.
+    struct CubeChunk {
+        int edge[6], face[12], cfield[8];
+        double w[8];
+    };
+    std::vector<CubeChunk> cube;
+    bool tune_rule_products = true;      // use `cube` where present (wke_tuning.rule_products)
     bool fused = false;
 
     double scale = 0;                    // 2^{1-d} (times 1/2 for omega = |k|^2)

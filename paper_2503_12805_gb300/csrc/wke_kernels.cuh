@@ -358,6 +358,7 @@ k_sep_planes_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase,
 // 256-entry slot and writes them to `work`; after one barrier it transforms
 // 4 consecutive columns (lane = column + 4 t holding j2 = t + 8 e) for every
 // pair of the row value and stores them.
+
 template <int N> struct SepWork64 {
     static constexpr int WP = N + 4;   // row pitch of `work` (= 4 mod 16: conflict-free column reads per half-warp)
 };
@@ -1206,24 +1207,56 @@ k_products_staged(const cx<T> *__restrict__ H, const cx<T> *__restrict__ Vtab, c
 // its point, the products of all groups of the chunk from the field slots,
 // with the same algebra and summation order as k_products_staged.  The
 // chunk's product table arrives as a kernel parameter.
-// Add a point's chunk total to its FP64 accumulators; in the last chunk of an
-// evaluation (Qout not null) write Q = scale * total instead (and Im Q when
-// Qiout is not null) and clear the accumulators for the next evaluation,
-// which is what the finalize kernel does for the other layouts.
+// Add a point's chunk total (sum, comp: a compensated sum) to its
+// accumulator; in the last chunk of an evaluation (Qout not null) write
+// Q = scale * total instead (and Im Q when Qiout is not null) and clear the
+// accumulators for the next evaluation, which is what the finalize kernel
+// does for the other layouts.  FP64 plans keep one double per point.  FP32
+// plans keep a float pair (hi, lo) in the same 8 bytes: hi takes the chunk
+// totals by Neumaier's compensated addition and lo gathers the rounding
+// errors and the chunks' compensations, so hi + lo carries about twice the
+// FP32 significand over the chunks; no FP64 instruction is needed.
+__device__ __forceinline__ float2 pair_add(float2 a, float s, float c) {
+    const float t = a.x + s;
+    const float e = fabsf(a.x) >= fabsf(s) ? (a.x - t) + s : (s - t) + a.x;
+    return make_float2(t, a.y + (e + c));
+}
+
 template <typename T>
-__device__ __forceinline__ void fused_epilogue(double *__restrict__ Qacc, double *__restrict__ Qim, size_t idx,
-                                               double add, double add_im, bool im, T *__restrict__ Qout,
+__device__ __forceinline__ void fused_epilogue(double *__restrict__ Qacc, double *__restrict__ Qim, size_t idx, T sum,
+                                               T comp, T sumi, T compi, bool im, T *__restrict__ Qout,
                                                T *__restrict__ Qiout, double scale) {
-    if (Qout) {
-        Qout[idx] = (T)(scale * (Qacc[idx] + add));
-        Qacc[idx] = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        float2 *A = reinterpret_cast<float2 *>(Qacc), *Ai = reinterpret_cast<float2 *>(Qim);
+        const float2 a = pair_add(A[idx], sum, comp);
+        if (Qout) {
+            Qout[idx] = (float)scale * (a.x + a.y);      // scale is a power of two
+            A[idx] = make_float2(0.f, 0.f);
+        } else {
+            A[idx] = a;
+        }
         if (im) {
-            if (Qiout) Qiout[idx] = (T)(scale * (Qim[idx] + add_im));
-            Qim[idx] = 0.0;
+            const float2 ai = pair_add(Ai[idx], sumi, compi);
+            if (Qout) {
+                if (Qiout) Qiout[idx] = (float)scale * (ai.x + ai.y);
+                Ai[idx] = make_float2(0.f, 0.f);
+            } else {
+                Ai[idx] = ai;
+            }
         }
     } else {
-        Qacc[idx] += add;
-        if (im) Qim[idx] += add_im;
+        const double add = (double)sum + (double)comp, add_im = (double)sumi + (double)compi;
+        if (Qout) {
+            Qout[idx] = (T)(scale * (Qacc[idx] + add));
+            Qacc[idx] = 0.0;
+            if (im) {
+                if (Qiout) Qiout[idx] = (T)(scale * (Qim[idx] + add_im));
+                Qim[idx] = 0.0;
+            }
+        } else {
+            Qacc[idx] += add;
+            if (im) Qim[idx] += add_im;
+        }
     }
 }
 
@@ -1330,7 +1363,7 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
             sumi = tsum;
         }
     }
-    fused_epilogue(Qacc, Qim, idx, (double)sum + (double)comp, (double)sumi + (double)compi, IM, Qout, Qiout, scale);
+    fused_epilogue<T>(Qacc, Qim, idx, sum, comp, sumi, compi, IM, Qout, Qiout, scale);
 }
 
 // Fused axis-0 transform and product pass for N = 64 in FP32.  A block holds
@@ -1361,7 +1394,21 @@ struct Fused64Tab {
     unsigned char pla[kMaxUnits], plb[kMaxUnits];  // separable plans: pair plane of each unit's fields
 };
 
-template <bool SEP, bool IM, bool NYQ, int PPGC, int NGC, bool EQW>
+// P += A B, U += A + B (complex).
+__device__ __forceinline__ void pu_acc(float2 &P, float2 &U, float2 A, float2 B) {
+    P.x = fmaf(A.x, B.x, P.x);
+    P.x = fmaf(-A.y, B.y, P.x);
+    P.y = fmaf(A.x, B.y, P.y);
+    P.y = fmaf(A.y, B.x, P.y);
+    U = cadd<float>(U, cadd<float>(A, B));
+}
+
+// CUBE: the cube rule's schedule (3 products per group, 8 groups, one weight
+// per group).  tab.oa[2 i + s] is the edge field of axis i (s = 1: negative),
+// tab.ob[4 i + q] the face field with component i zero (q's bit 0: the lower
+// other axis negative, bit 1: the higher one), tab.oc[v] and tab.w[v] the C
+// field and weight of the group of vertex v (bit a: v_a < 0).
+template <bool SEP, bool IM, bool NYQ, int PPGC, int NGC, bool EQW, bool CUBE>
 __global__ void __launch_bounds__(256, 3)
 k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const float2 *__restrict__ Vtab,
           const float *__restrict__ f, double *__restrict__ Qacc, double *__restrict__ Qim,
@@ -1452,8 +1499,46 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
     const int ppg = PPGC > 0 ? PPGC : PPG;
     const int ngr = NGC > 0 ? NGC : ng;
     float sum = 0.f, comp = 0.f, sumi = 0.f, compi = 0.f;
+    if constexpr (CUBE) {
+        // axis by axis: the two edge fields of axis i meet its four face
+        // fields, each pair a product of the vertex they agree with, so that
+        // every field is read once per point; P = sum A B and U = sum (A + B)
+        // per group in registers
+        float2 Pq[8], Uq[8];
 #pragma unroll
-    for (int g = 0; g < ngr; ++g) {
+        for (int v = 0; v < 8; ++v) Pq[v] = Uq[v] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
+            const float2 Ep = *reinterpret_cast<const float2 *>(fb + off(tab.oa[2 * i]));
+            const float2 Em = *reinterpret_cast<const float2 *>(fb + off(tab.oa[2 * i + 1]));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 Fc = *reinterpret_cast<const float2 *>(fb + off(tab.ob[4 * i + q]));
+                const int vp = ((q & 1) << j) | ((q >> 1) << k), vm = vp | (1 << i);
+                pu_acc(Pq[vp], Uq[vp], Ep, Fc);
+                pu_acc(Pq[vm], Uq[vm], Em, Fc);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const float2 C = *reinterpret_cast<const float2 *>(fb + off(tab.oc[v]));
+            const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
+            const float w = tab.w[v];
+            const float acc = w * ((sr * Pq[v].x - si * Pq[v].y) - (cr * Uq[v].x - ci * Uq[v].y));
+            float tsum = sum + acc;
+            comp += fabsf(sum) >= fabsf(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+            sum = tsum;
+            if (IM) {
+                const float acci = w * ((sr * Pq[v].y + si * Pq[v].x) - (cr * Uq[v].y + ci * Uq[v].x));
+                tsum = sumi + acci;
+                compi += fabsf(sumi) >= fabsf(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+                sumi = tsum;
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < (CUBE ? 0 : ngr); ++g) {
         const float2 C = *reinterpret_cast<const float2 *>(fb + off(tab.oc[g]));
         const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
         float acc = 0.f, acci = 0.f;
@@ -1496,7 +1581,7 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
             sumi = tsum;
         }
     }
-    fused_epilogue(Qacc, Qim, idx, (double)sum + (double)comp, (double)sumi + (double)compi, IM, Qout, Qiout, scale);
+    fused_epilogue<float>(Qacc, Qim, idx, sum, comp, sumi, compi, IM, Qout, Qiout, scale);
 }
 
 // ------------------------------------------------------------------ finalize
@@ -1519,6 +1604,19 @@ __global__ void k_finalize(double *__restrict__ Qacc, double *__restrict__ Qim, 
             }
             if (Qi) Qi[i] = (T)(scale * si);
         }
+    }
+}
+
+// Finalize of the FP32 fused layouts' (hi, lo) accumulator pairs (one
+// accumulator): Q = scale * (hi + lo) into a double grid; the pairs are
+// cleared.
+template <typename TQ>
+__global__ void k_finalize_pair(double *__restrict__ Qacc, size_t ND, double scale, TQ *__restrict__ Q) {
+    float2 *A = reinterpret_cast<float2 *>(Qacc);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ND; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = A[i];
+        Q[i] = (TQ)(scale * ((double)a.x + (double)a.y));
+        A[i] = make_float2(0.f, 0.f);
     }
 }
 

@@ -329,21 +329,36 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
             for (int g = 0; g < cr.ng && eqw; ++g)
                 for (int q = 1; q < PPGC; ++q) eqw = eqw && t64.w[g * PPGC + q] == t64.w[g * PPGC];
             int rc = 0;
-#define WKE_F64_LAUNCH(NGC_, EQW_)                                                                              \
+#define WKE_F64_LAUNCH(NGC_, EQW_, CUBE_)                                                                       \
     do {                                                                                                        \
-        if ((rc = set_smem(k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_>, smem64))) return rc;                       \
-        k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_><<<(N * N) / 4, kF64Pts, smem64, s>>>(                          \
+        if ((rc = set_smem(k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_, CUBE_>, smem64))) return rc;                \
+        k_fused64<SEP, IM, NYQ, PPGC, NGC_, EQW_, CUBE_><<<(N * N) / 4, kF64Pts, smem64, s>>>(                   \
             static_cast<const float2 *>(SEP ? p.S : p.H), static_cast<const float4 *>(p.unit_e0),                 \
             static_cast<const float2 *>(p.V), static_cast<const float *>(p.f), p.Qacc, p.Qacc_im,                \
             static_cast<const float2 *>(p.tw), cr.sK, cr.ng, hp.products_per_group, nplanes, ubase, t64,          \
             static_cast<float *>(p.Qout), static_cast<float *>(p.Qiout), p.scale_out);                          \
     } while (0)
+            if constexpr (PPGC == 3) {
+                if (!hp.cube.empty() && hp.tune_rule_products) {
+                    // the cube rule's schedule: every field read once per point
+                    const HostPlan::CubeChunk &cu = hp.cube[c];
+                    const unsigned sb = kF64Pts * sizeof(float2);
+                    for (int i = 0; i < 6; ++i) t64.oa[i] = (unsigned)cu.edge[i] * sb;
+                    for (int i = 0; i < 12; ++i) t64.ob[i] = (unsigned)cu.face[i] * sb;
+                    for (int v = 0; v < 8; ++v) {
+                        t64.oc[v] = (unsigned)cu.cfield[v] * sb;
+                        t64.w[v] = (float)cu.w[v];
+                    }
+                    WKE_F64_LAUNCH(8, true, true);
+                    return (int)cudaGetLastError();
+                }
+            }
             if constexpr (PPGC == 3 || PPGC == 4) {
-                if (cr.ng == 8 && eqw) WKE_F64_LAUNCH(8, true);
-                else if (cr.ng == 8) WKE_F64_LAUNCH(8, false);
-                else WKE_F64_LAUNCH(0, false);
+                if (cr.ng == 8 && eqw) WKE_F64_LAUNCH(8, true, false);
+                else if (cr.ng == 8) WKE_F64_LAUNCH(8, false, false);
+                else WKE_F64_LAUNCH(0, false, false);
             } else {
-                WKE_F64_LAUNCH(0, false);
+                WKE_F64_LAUNCH(0, false, false);
             }
 #undef WKE_F64_LAUNCH
             return (int)cudaGetLastError();
@@ -671,7 +686,10 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     const int threads = 256;
     const int blocks = (int)std::min<size_t>((ND + threads - 1) / threads, num_sms() * 8);
     double *qf = static_cast<double *>(p.map0);
-    k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, n_accumulators(hp), ND, hp.scale, qf, nullptr);
+    if (hp.fused)   // FP32 fused layouts accumulate in (hi, lo) float pairs
+        k_finalize_pair<double><<<blocks, threads, 0, s>>>(p.Qacc, ND, hp.scale, qf);
+    else
+        k_finalize<double><<<blocks, threads, 0, s>>>(p.Qacc, nullptr, n_accumulators(hp), ND, hp.scale, qf, nullptr);
     int rc = (int)cudaGetLastError();
     const int n = hp.N, m = hp.N_in;
     const double2 *K = static_cast<const double2 *>(p.Kproj);

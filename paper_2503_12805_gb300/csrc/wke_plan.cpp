@@ -316,6 +316,91 @@ static int build_shared_layout(HostPlan &hp, bool force) {
     return WKE_OK;
 }
 
+// Recognise the cube rule's structure in every chunk (HostPlan::cube).  The
+// fields' shifts are classified by the signs of their components, each
+// relative to the chunk's largest component (equal within 1e-9); a group
+// matches when its C field is a vertex v, its three products are each one
+// edge and one face field of v for distinct axes, and the three weights are
+// equal.
+static void build_cube_schedule(HostPlan &hp) {
+    hp.cube.clear();
+    if (!(hp.shared && hp.d == 3 && hp.N == 64 && hp.products_per_group == 3)) return;   // k_fused64's schedule
+    std::vector<HostPlan::CubeChunk> tabs(hp.n_chunks);
+    for (int c = 0; c < hp.n_chunks; ++c) {
+        const int g0 = hp.chunk_g0[c], g1 = hp.chunk_g0[c + 1], f0 = hp.chunk_f0[c], K = hp.chunk_f0[c + 1] - f0;
+        if (g1 - g0 != 8 || K != 26) return;
+        double m = 0.0;
+        for (int l = 0; l < K; ++l)
+            for (int a = 0; a < 3; ++a) m = std::max(m, std::fabs(hp.field_shift[(size_t)(f0 + l) * 3 + a]));
+        if (!(m > 0.0)) return;
+        std::vector<int> sg(3 * K), nz(K, 0);
+        for (int l = 0; l < K; ++l)
+            for (int a = 0; a < 3; ++a) {
+                const double x = hp.field_shift[(size_t)(f0 + l) * 3 + a] / m;
+                if (std::fabs(x) <= 1e-9) sg[3 * l + a] = 0;
+                else if (std::fabs(x - 1.0) <= 1e-9) sg[3 * l + a] = 1;
+                else if (std::fabs(x + 1.0) <= 1e-9) sg[3 * l + a] = -1;
+                else return;
+                nz[l] += sg[3 * l + a] != 0;
+            }
+        HostPlan::CubeChunk &t = tabs[c];
+        std::fill(std::begin(t.edge), std::end(t.edge), -1);
+        std::fill(std::begin(t.face), std::end(t.face), -1);
+        std::fill(std::begin(t.cfield), std::end(t.cfield), -1);
+        auto zero_axis = [&](int l) {
+            for (int a = 0; a < 3; ++a)
+                if (sg[3 * l + a] == 0) return a;
+            return -1;
+        };
+        auto nonzero_axis = [&](int l) {
+            for (int a = 0; a < 3; ++a)
+                if (sg[3 * l + a] != 0) return a;
+            return -1;
+        };
+        for (int l = 0; l < K; ++l) {
+            if (nz[l] == 1) {
+                const int i = nonzero_axis(l);
+                int &e = t.edge[2 * i + (sg[3 * l + i] < 0)];
+                if (e >= 0) return;
+                e = l;
+            } else if (nz[l] == 2) {
+                const int i = zero_axis(l), j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
+                int &f = t.face[4 * i + (sg[3 * l + j] < 0) + 2 * (sg[3 * l + k] < 0)];
+                if (f >= 0) return;
+                f = l;
+            }
+        }
+        for (int g = g0; g < g1; ++g) {
+            const int cf = hp.group_cfield[g];
+            if (nz[cf] != 3) return;
+            const int v = (sg[3 * cf] < 0) + 2 * (sg[3 * cf + 1] < 0) + 4 * (sg[3 * cf + 2] < 0);
+            if (t.cfield[v] >= 0) return;
+            t.cfield[v] = cf;
+            t.w[v] = hp.prod_W[(size_t)g * 3];
+            int axes = 0;
+            for (int q = 0; q < 3; ++q) {
+                const size_t slot = (size_t)g * 3 + q;
+                if (hp.prod_W[slot] != t.w[v]) return;
+                int fe = hp.prod_fa[slot], ff = hp.prod_fb[slot];
+                if (nz[fe] == 2) std::swap(fe, ff);
+                if (nz[fe] != 1 || nz[ff] != 2) return;
+                const int i = nonzero_axis(fe);
+                if (zero_axis(ff) != i || (axes >> i) & 1) return;
+                axes |= 1 << i;
+                for (int a = 0; a < 3; ++a)
+                    if ((a == i ? sg[3 * fe + a] : sg[3 * ff + a]) != sg[3 * cf + a]) return;
+            }
+        }
+        for (int i = 0; i < 6; ++i)
+            if (t.edge[i] < 0) return;
+        for (int i = 0; i < 12; ++i)
+            if (t.face[i] < 0) return;
+        for (int i = 0; i < 8; ++i)
+            if (t.cfield[i] < 0) return;
+    }
+    hp.cube = tabs;
+}
+
 // Separable transforms (3D, shared-field layout; see HostPlan::separable).
 // Row values and pairs are equal when they agree to 1e-12 (relative), as
 // fields are; the first field with a value supplies its phase row.  With
@@ -627,6 +712,7 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
         hp.can_fuse = hp.groups_per_chunk <= kFusedMaxGroups && maxp <= kFusedMaxProducts &&
                       hp.max_chunk_fields <= 255 && fused_smem_bytes(hp.N, hp.max_chunk_fields) <= 227 * 1024;
         hp.fused = hp.can_fuse;
+        if (hp.can_fuse) build_cube_schedule(hp);
     }
     if (hp.shared) {
         hp.chunk_u0.assign(1, 0);

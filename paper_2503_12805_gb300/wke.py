@@ -58,7 +58,7 @@ class WkeQuadrature(ctypes.Structure):
 
 class WkeTuning(ctypes.Structure):
     _fields_ = [("pass2_points_per_thread", ctypes.c_int), ("pass1_units_per_block", ctypes.c_int),
-                ("fuse_products", ctypes.c_int), ("forward_fp32", ctypes.c_int)]
+                ("fuse_products", ctypes.c_int), ("forward_fp32", ctypes.c_int), ("rule_products", ctypes.c_int)]
 
 
 class WkeRequest(ctypes.Structure):
@@ -83,7 +83,7 @@ class WkePlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t), ("N_compute", ctypes.c_int), ("shared_fields", ctypes.c_int),
         ("units_per_collision", ctypes.c_int), ("separable", ctypes.c_int),
         ("pair_planes_per_collision", ctypes.c_int), ("fused_products", ctypes.c_int),
-        ("row_values_per_collision", ctypes.c_int),
+        ("row_values_per_collision", ctypes.c_int), ("rule_products_available", ctypes.c_int),
     ]
 
 
@@ -239,14 +239,21 @@ def wke_plan_get_tuning(plan) -> WkeTuning:
 
 
 def wke_plan_set_tuning(plan, pass2_points_per_thread: int, pass1_units_per_block: int = 0,
-                        fuse_products: int | None = None, forward_fp32: int | None = None) -> None:
-    """Set the launch layout; fuse_products / forward_fp32 None keep the plan's current choice."""
+                        fuse_products: int | None = None, forward_fp32: int | None = None,
+                        rule_products: int | None = None) -> None:
+    """Set the launch layout; fuse_products / forward_fp32 / rule_products None keep the plan's
+    current choice (rule_products: the plan's rule schedule whenever the products are fused)."""
     cur = wke_plan_get_tuning(plan)
     if fuse_products is None:
         fuse_products = cur.fuse_products
     if forward_fp32 is None:
         forward_fp32 = cur.forward_fp32
-    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block, fuse_products, forward_fp32)
+    if rule_products is None:
+        if cur.fuse_products and fuse_products:
+            rule_products = cur.rule_products
+        else:
+            rule_products = 1 if fuse_products and wke_plan_get_info(plan).rule_products_available else 0
+    t = WkeTuning(pass2_points_per_thread, pass1_units_per_block, fuse_products, forward_fp32, rule_products)
     _check(lib().wke_plan_set_tuning(plan, ctypes.byref(t)))
 
 

@@ -149,10 +149,14 @@ def test_shared_field_layout_counts(wke):
     assert info.fused_products == 1
     # (no finalize launch: the last chunk's product kernel writes Q)
     assert info.launches_per_collision == 3 + 3 * 32         # forward: rows, axis 1, axis 0
+    # every radius has the cube rule's structure: 6 edge, 12 face and 8 vertex shifts, each
+    # group pairing its vertex's edge and face fields axis by axis
+    assert info.rule_products_available == 1
     fp64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP64)
     assert fp64.units_per_collision == 32 * 13            # a whole radius fits the FP64 budget
     assert fp64.separable == 1 and fp64.fused_products == 0
     assert fp64.launches_per_collision == 3 + 4 * 32 + 1
+    assert fp64.rule_products_available == 0             # no fused kernel in FP64
     unsep = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, layout=wke.WKE_LAYOUT_SHARED)
     assert unsep.separable == 0 and unsep.fused_products == 1 and unsep.pair_planes_per_collision == 0
     assert unsep.units_per_collision == 32 * 13
@@ -160,7 +164,11 @@ def test_shared_field_layout_counts(wke):
     assert per_group.shared_fields == 0 and per_group.units_per_collision == 256 * 3 + 128
     # with the Nyquist modes zeroed F is not the grid interpolant: no product vanishes
     zero = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32, nyquist=wke.WKE_NYQ_ZERO)
-    assert zero.products_per_group == 4
+    assert zero.products_per_group == 4 and zero.rule_products_available == 0
+    ico = _describe(wke, 3, 64, 2, 12, 20, precision=wke.WKE_FP32)   # icosahedron / dodecahedron
+    assert ico.rule_products_available == 0
+    n32 = _describe(wke, 3, 32, 4, 8, 8, precision=wke.WKE_FP32)
+    assert n32.fused_products == 1 and n32.rule_products_available == 0   # the N = 64 kernel only
     # 2D mid-point 4 x 4: 8 distinct fields per radius, 1 product per group
     two_d = _describe(wke, 2, 128, 32, 4, 4, precision=wke.WKE_FP32)
     assert two_d.shared_fields == 1 and two_d.products_per_group == 1 and two_d.units_per_collision == 32 * 4
