@@ -357,7 +357,13 @@ k_sep_planes_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase,
 // plane (lane = row + 4 t holding j3 = t + 8 e) with line64_swz in its own
 // 256-entry slot and writes them to `work`; after one barrier it transforms
 // 4 consecutive columns (lane = column + 4 t holding j2 = t + 8 e) for every
-// pair of the row value and stores them.
+// pair of the row value and stores them.  Its planes are column-blocked:
+// point (i2, i3) of a plane at sep_col64(i2 * 64 + i3), blocks of 4 columns
+// one after the other, each 64 rows of 4 points: every store instruction
+// writes 256 contiguous bytes.
+__host__ __device__ __forceinline__ int sep_col64(int col) {
+    return ((col & 63) >> 2) * 256 + (col >> 6) * 4 + (col & 3);
+}
 
 template <int N> struct SepWork64 {
     static constexpr int WP = N + 4;   // row pitch of `work` (= 4 mod 16: conflict-free column reads per half-warp)
@@ -400,7 +406,9 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
         const int pf = sep_p[p0 + p];
         if (!WKE_GUARD(pf >= 0 && pf < n_fields, kChkSepPair)) continue;
         const float2 *e1 = phase + (size_t)pf * 3 * N + N;
-        float2 *out = S + ((size_t)p * N + j1) * NN;
+        // column-blocked plane (sep_col64): this warp's 4 columns are one
+        // contiguous 64 x 4 block, so each store instruction writes 256 bytes
+        float2 *out = S + ((size_t)p * N + j1) * NN + (size_t)warp * 4 * N;
         {
             const int i3 = 4 * warp + c;
             float2 x[8];
@@ -409,7 +417,7 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
             line64_swz(x, c, t, slot, tws);
             __syncwarp();
 #pragma unroll
-            for (int e = 0; e < 8; ++e) out[(t + 8 * e) * N + i3] = x[e];
+            for (int e = 0; e < 8; ++e) out[(t + 8 * e) * 4 + c] = x[e];
         }
     }
 }
@@ -832,7 +840,9 @@ k_axis0_sep(const cx<T> *__restrict__ S, const cx<T> *__restrict__ phase, const 
     const size_t ND = (size_t)N * P;
     const int qa = field_pair[fa], qb = field_pair[fb];
     if (!WKE_GUARD(qa >= 0 && qa < max_pairs && qb >= 0 && qb < max_pairs, kChkAxis0Unit)) return;
-    const cx<T> *sa = S + (size_t)qa * ND + col, *sb = S + (size_t)qb * ND + col;
+    // the FP32 N = 64 planes are column-blocked (k_sep_planes64)
+    const int scol = (N == 64 && sizeof(T) == 4) ? sep_col64(col) : col;
+    const cx<T> *sa = S + (size_t)qa * ND + scol, *sb = S + (size_t)qb * ND + scol;
     const cx<T> *ea = phase + (size_t)fa * 3 * N, *eb = phase + (size_t)fb * 3 * N;
     cx<T> v[E];
 #pragma unroll
@@ -1299,7 +1309,9 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
         cx<T> v[E];
         if (SEP) {
             const int fb = pair ? fa + 1 : fa;
-            const cx<T> *sa = src + (size_t)field_pair[fa] * ND + col, *sb = src + (size_t)field_pair[fb] * ND + col;
+            // the FP32 N = 64 planes are column-blocked (k_sep_planes64)
+            const int scol = (N == 64 && sizeof(T) == 4) ? sep_col64(col) : col;
+            const cx<T> *sa = src + (size_t)field_pair[fa] * ND + scol, *sb = src + (size_t)field_pair[fb] * ND + scol;
             const cx<T> *ea = phase + (size_t)fa * 3 * N, *eb = phase + (size_t)fb * 3 * N;
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = sep_input<T>(sa, sb, ea, eb, t + e * TPL, P, pair);
@@ -1429,7 +1441,8 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
     // ---- stage the planes: 128 pieces of 16 bytes per plane, two planes per pass
     {
         const int j1 = (tid >> 1) & 63, h = tid & 1;
-        const float2 *sp = src + (size_t)j1 * P + col0 + 2 * h;
+        // separable plans: column-blocked pair planes (sep_col64); pass-1 units: row-major
+        const float2 *sp = src + (size_t)j1 * P + (SEP ? sep_col64(col0) : col0) + 2 * h;
         float2 *dp = pst + j1 * CB + 2 * h;
         for (int pl = tid >> 7; pl < nplanes; pl += 2) cp_async16(dp + (size_t)pl * PTS, sp + (size_t)pl * ND);
     }
