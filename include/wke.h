@@ -235,6 +235,17 @@ int wke_collision(wke_plan *plan, const void *f_dev, void *Q_dev, void *stream);
 int wke_collision_ex(wke_plan *plan, const void *f_dev, void *Q_dev, void *Qim_dev,
                      void *stream);
 
+/* As wke_collision, then the Fourier coefficients of Q (Algorithm 1's Q-hat
+ * before its final inverse transform; Eq. (3.1) applied to Q):
+ *   Qhat_j = N^{-d} sum_i Q_i exp(-i pi j.k_i / L),  j in [-N/2, N/2-1]^d,
+ * one forward transform of the grid values (computed in double), stored in
+ * DFT order (mode j at position j mod N per axis) as N^d interleaved
+ * (re, im) pairs of the plan's precision.  Q_dev (N^d values) and Qhat_dev
+ * (2 N^d values) are device buffers owned by the caller and must not
+ * overlap f_dev or each other.  Stream-ordered like wke_collision.
+ * Errors: WKE_ERR_INVALID for NULL or overlapping buffers, WKE_ERR_CUDA. */
+int wke_collision_spectrum(wke_plan *plan, const void *f_dev, void *Q_dev, void *Qhat_dev, void *stream);
+
 /* End-to-end variant with host buffers: copies f_host to plan-owned device
  * memory, evaluates, copies Q back to Q_host and synchronises the plan's
  * stream before returning.  Pinned host memory gives full copy bandwidth. */

@@ -20,6 +20,7 @@ template <typename T> int pass1_T(const HostPlan &, const DevicePtrs &, int, cud
 template <typename T> int nyquist_T(const HostPlan &, const DevicePtrs &, int, cudaStream_t);
 template <typename T> int pass2_T(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);
 template <typename T> int finalize_T(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);
+template <typename T> int spectrum_T(const HostPlan &, const DevicePtrs &, const void *, void *, cudaStream_t);
 template <typename T> int moments_T(const HostPlan &, const void *, double *, double *, cudaStream_t);
 template <typename T>
 int rk_stage_T(const HostPlan &, const void *, const void *, double *, void *, double, double, int, cudaStream_t);
@@ -686,6 +687,26 @@ int wke_collision_ex(wke_plan *plan, const void *f, void *Q, void *Qim, void *st
 int wke_collision(wke_plan *plan, const void *f, void *Q, void *stream) {
     NvtxRange nvtx_range("wke_collision");
     return wke_collision_ex(plan, f, Q, nullptr, stream);
+}
+
+int wke_collision_spectrum(wke_plan *plan, const void *f, void *Q, void *Qhat, void *stream) {
+    NvtxRange nvtx_range("wke_collision_spectrum");
+    if (!plan || !f || !Q || !Qhat) return fail(WKE_ERR_INVALID, "plan, f, Q and Qhat must be non-NULL");
+    const size_t es = plan->hp.precision == WKE_FP64 ? 8 : 4, n = grid_in_elems(plan->hp);
+    auto overlap = [](const void *a, size_t na, const void *b, size_t nb) {
+        const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+        return x < y + nb && y < x + na;
+    };
+    if (overlap(f, n * es, Q, n * es) || overlap(f, n * es, Qhat, 2 * n * es) || overlap(Q, n * es, Qhat, 2 * n * es))
+        return fail(WKE_ERR_INVALID, "f, Q and Qhat must not overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = collision(plan, f, Q, nullptr, s);
+    if (rc) return rc;
+    // ordered after the evaluation on `s`, whose forward scratch it reuses
+    rc = plan->hp.precision == WKE_FP64 ? spectrum_T<double>(plan->hp, plan->dp, Q, Qhat, s)
+                                        : spectrum_T<float>(plan->hp, plan->dp, Q, Qhat, s);
+    if (rc) return cuda_fail(static_cast<cudaError_t>(rc), "Q-hat transform");
+    return WKE_OK;
 }
 
 int wke_collision_host(wke_plan *plan, const void *f_host, void *Q_host) {

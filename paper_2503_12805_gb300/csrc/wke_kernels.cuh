@@ -180,6 +180,22 @@ __global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict_
     }
 }
 
+// Q-hat: multiply the DFT-order coefficients by (-1)^{j_1 + ... + j_d}, the
+// factor exp(-i pi j.k_0 / L) of the grid's first point k_0 = (-L, ..., -L)
+// (the parity of the signed mode j equals that of its position, N even).
+template <typename T>
+__global__ void k_alternate_sign(cx<T> *__restrict__ g, int d, int N, size_t nd) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x) {
+        size_t r = i;
+        int par = 0;
+        for (int a = 0; a < d; ++a) {
+            par += (int)(r % (size_t)N);
+            r /= (size_t)N;
+        }
+        if (par & 1) g[i] = mkc<T>(-g[i].x, -g[i].y);
+    }
+}
+
 // ------------------------------------------------------------------ pass 1
 // Global field indices (fa, fb) of unit u of the chunk starting at group g0
 // with ng groups; fb = -1 for a lone field.  In the shared-field layout

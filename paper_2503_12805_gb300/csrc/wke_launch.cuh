@@ -117,6 +117,60 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
     return forward_nc<T, N, double>(hp, p, s);
 }
 
+// Q-hat of grid values Q (N_in grid, plan type T) into Qhat: the forward
+// transform's three (two in 2D) line passes in double on the plan's forward
+// scratch, normalised by N^-d, then the alternating sign of the grid offset.
+template <typename T, int N>
+static int spectrum_n(const HostPlan &hp, const DevicePtrs &p, const void *Q, void *Qhat, cudaStream_t s) {
+    typedef double TC;
+    typedef LineCfg<TC, N> Cfg;
+    const int P = hp.d == 2 ? N : N * N;
+    cx<TC> *tmp = static_cast<cx<TC> *>(p.fwd_tmp);
+    const cx<TC> *tw = reinterpret_cast<const cx<TC> *>(p.tw64);
+    int rc = 0;
+    if (hp.d == 3) {
+        if constexpr (N <= 64) {
+            const int rows = N * N;
+            const int warps = spread_warps<N>(rows);
+            const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
+            k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(Q),
+                                                                                       tmp, tw);
+            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, smem))) return rc;
+            k_fwd_mid_3d<N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
+        } else {
+            return (int)cudaErrorInvalidValue;
+        }
+    } else {
+        const int warps = spread_warps<N>(N);
+        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+        if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
+        k_fwd_rows_2d<T, N, TC><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(Q), tmp, tw);
+    }
+    const int warps = spread_warps<N>(P);
+    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+    if ((rc = set_smem(k_fwd_cols<T, N, TC>, smem))) return rc;
+    const size_t nd = (size_t)N * P;
+    k_fwd_cols<T, N, TC><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, static_cast<cx<T> *>(Qhat), tw, P,
+                                                                         hp.d, 1.0 / (double)nd, 0, nullptr);
+    const int blocks = (int)std::min<size_t>((nd + 255) / 256, (size_t)num_sms() * 8);
+    k_alternate_sign<T><<<blocks, 256, 0, s>>>(static_cast<cx<T> *>(Qhat), hp.d, N, nd);
+    return (int)cudaGetLastError();
+}
+
+template <typename T> int spectrum_T(const HostPlan &hp, const DevicePtrs &p, const void *Q, void *Qhat, cudaStream_t s) {
+    switch (hp.N_in) {
+        case 16: return spectrum_n<T, 16>(hp, p, Q, Qhat, s);
+        case 32: return spectrum_n<T, 32>(hp, p, Q, Qhat, s);
+        case 48: return spectrum_n<T, 48>(hp, p, Q, Qhat, s);
+        case 64: return spectrum_n<T, 64>(hp, p, Q, Qhat, s);
+        case 96: return spectrum_n<T, 96>(hp, p, Q, Qhat, s);
+        case 128: return spectrum_n<T, 128>(hp, p, Q, Qhat, s);
+        case 256: return spectrum_n<T, 256>(hp, p, Q, Qhat, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
 // ------------------------------------------------------------------ pass 1
 // Groups, fields and units of chunk c: per-group layout (g0, ng; sf0 = -1)
 // or shared-field layout (fields sf0 .. sf0 + sK - 1).
@@ -715,6 +769,7 @@ template <typename T> int dealias_finish_T(const HostPlan &hp, const DevicePtrs 
     template int dealias_prepare_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                 \
     template int dealias_finish_T<T>(const HostPlan &, const DevicePtrs &, void *, void *, cudaStream_t);  \
     template int forward_T<T>(const HostPlan &, const DevicePtrs &, cudaStream_t);                         \
+    template int spectrum_T<T>(const HostPlan &, const DevicePtrs &, const void *, void *, cudaStream_t);  \
     template int pass1_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                      \
     template int nyquist_T<T>(const HostPlan &, const DevicePtrs &, int, cudaStream_t);                    \
     template int pass2_T<T>(const HostPlan &, const DevicePtrs &, int, bool, cudaStream_t);                \

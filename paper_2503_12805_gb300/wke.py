@@ -90,7 +90,7 @@ class WkePlanInfo(ctypes.Structure):
 EXPORTED = [
     "wke_quadrature_default", "wke_plan_create", "wke_plan_destroy", "wke_plan_footprint_bytes",
     "wke_plan_get_info", "wke_plan_describe", "wke_plan_node_table", "wke_collision", "wke_collision_ex",
-    "wke_collision_host", "wke_plan_set_stream", "wke_step", "wke_moments",
+    "wke_collision_host", "wke_collision_spectrum", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
     "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_alu_peak", "wke_check_status",
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_collision": (i, [vp, vp, vp, vp]),
         "wke_collision_ex": (i, [vp, vp, vp, vp, vp]),
         "wke_collision_host": (i, [vp, vp, vp]),
+        "wke_collision_spectrum": (i, [vp, vp, vp, vp, vp]),
         "wke_plan_set_stream": (i, [vp, vp]),
         "wke_step": (i, [vp, vp, d, i]),
         "wke_moments": (i, [vp, vp, vp, vp]),
@@ -207,6 +208,10 @@ def wke_collision(plan, f_ptr: int, Q_ptr: int, stream: int = 0) -> None:
 
 def wke_collision_ex(plan, f_ptr: int, Q_ptr: int, Qim_ptr: int | None, stream: int = 0) -> None:
     _check(lib().wke_collision_ex(plan, f_ptr, Q_ptr, Qim_ptr, stream))
+
+
+def wke_collision_spectrum(plan, f_ptr: int, Q_ptr: int, Qhat_ptr: int, stream: int = 0) -> None:
+    _check(lib().wke_collision_spectrum(plan, f_ptr, Q_ptr, Qhat_ptr, stream))
 
 
 def wke_collision_host(plan, f_host_ptr: int, Q_host_ptr: int) -> None:
@@ -465,6 +470,22 @@ class Plan:
         wke_collision_ex(self.handle, f.data_ptr(), self._check_grid(Q).data_ptr(),
                          None if Qim is None else self._check_grid(Qim).data_ptr(), s)
         return Q
+
+    def spectrum(self, f, Q=None, Qhat=None, stream=None):
+        """Q and its Fourier coefficients Qhat (complex, DFT order; see
+        wke_collision_spectrum).  Returns (Q, Qhat)."""
+        import torch
+        self._check_grid(f)
+        if Q is None:
+            Q = torch.empty_like(f)
+        cdt = torch.complex128 if self.precision == "fp64" else torch.complex64
+        if Qhat is None:
+            Qhat = torch.empty((self.N,) * self.d, dtype=cdt, device=f.device)
+        if not (Qhat.is_cuda and Qhat.dtype == cdt and Qhat.is_contiguous() and tuple(Qhat.shape) == (self.N,) * self.d):
+            raise ValueError(f"expected a contiguous CUDA {cdt} tensor of shape {(self.N,) * self.d}")
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        wke_collision_spectrum(self.handle, f.data_ptr(), self._check_grid(Q).data_ptr(), Qhat.data_ptr(), s)
+        return Q, Qhat
 
     def step(self, f, dt: float, rk_stages: int = 4, stream=None):
         import torch

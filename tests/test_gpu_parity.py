@@ -185,6 +185,47 @@ def test_3d_n64_full_field_small_quadrature():
         assert rel_max_err(Q, ref) <= TOL[prec], prec
 
 
+@pytest.mark.parametrize("dealias", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 16), (3, 64)])
+def test_collision_spectrum(d, N, prec, dealias):
+    """Q-hat (Algorithm 1's coefficients before the final inverse transform):
+    the GPU's Q-hat against the oracle's Eq. (3.1) transform of the oracle's
+    Q, elementwise, relative to max |Q| (each coefficient is a mean of Q times
+    unit phases, so an error e max |Q| in Q moves it by at most that); Q
+    itself as wke_collision gives it; and the mode-0 coefficient equals the
+    grid mean of the GPU's own Q (to the output precision)."""
+    torch = require_cuda()
+    from paper_2503_12805_gb300 import wke
+    if dealias and (d, N) == (3, 64):
+        pytest.skip("the de-aliased plan of this case transforms on 128^3, outside the 3D lengths")
+    sph = "midpoint" if d == 2 else "cube"
+    n_r = 2 if N == 64 else 3
+    f = I.gaussian_noise(d, N, 8.0, 77, 0.2)
+    quad = _oracle_quad(d, 8.0, n_r, 4 if d == 2 else 8, 4 if d == 2 else 8, sph)
+    nyq = "zero" if dealias else "keep"
+    if dealias:
+        ref = O.collision_dealiased(f, 8.0, quad, nyquist=nyq)
+    else:
+        ref = O.collision_fast(f, 8.0, quad, nyquist=nyq)
+    ref = ref[0] if isinstance(ref, tuple) else ref
+    ref_hat = O.FFT(ref, 8.0)
+    kw = {"nyquist": nyq, "dealias": dealias}
+    with _plan(wke, d, N, 8.0, quad.n_r, quad.n_s, quad.n_sig, sph, precision=prec, **kw) as plan:
+        ft = torch.tensor(f, dtype=plan.dtype, device="cuda")
+        Q, Qhat = plan.spectrum(ft)
+        torch.cuda.synchronize()
+        Q, Qhat = Q.double().cpu().numpy(), Qhat.cpu().numpy().astype(np.complex128)
+        with pytest.raises(wke.WkeError):
+            plan.spectrum(ft, Q=ft)                    # Q may not overlap f
+    tol = TOL[prec] if prec == "fp64" else max(TOL[prec], fp32_tolerance(f, 8.0, quad, dealias=dealias,
+                                                                           nyquist=nyq))
+    scale = np.max(np.abs(ref))
+    assert rel_max_err(Q, ref) <= tol
+    assert np.max(np.abs(Qhat - ref_hat)) / scale <= tol
+    assert abs(Qhat.flat[0] - Q.mean()) <= (1e-12 if prec == "fp64" else 1e-6) * np.max(np.abs(Q))
+
+
 @pytest.mark.parametrize("d,N", [(2, 32), (3, 16)])
 def test_nyquist_zero_mode(d, N):
     torch = require_cuda()
