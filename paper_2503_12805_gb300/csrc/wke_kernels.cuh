@@ -560,6 +560,90 @@ k_nyquist_3d(const cx<T> *__restrict__ phase, cx<T> *__restrict__ V, const cx<T>
     for (int e = 0; e < E; ++e) out[(ty + e * TPL) * N + z] = v[e];
 }
 
+// The same tables for N = 64 in FP32 with warp-local lines (the layout of
+// k_sep_planes64): block (axis, unit), 512 threads.  The block first copies
+// the axis's Nyquist slice (64 x 64, rows padded to WP) and the two fields'
+// phase rows into shared memory with cp.async; then warp w forms the input of
+// rows 4 w .. 4 w + 3 (lane = row + 4 t holding columns t + 8 e), transforms
+// them with line64_swz in its own slot and writes them to `work`; after one
+// barrier it transforms columns 4 w .. 4 w + 3 and stores the table.
+template <int N>
+__global__ void __launch_bounds__(512, 1)
+k_nyquist64(const float2 *__restrict__ phase, float2 *__restrict__ V, const float2 *__restrict__ tw_g,
+            const float2 *__restrict__ nslice, const int *__restrict__ prod_local, int G, int n_groups, int FPG,
+            int PPG, int units_per_chunk, int chunk0, int sf0, int sK) {
+    static_assert(N == 64, "64-point lines");
+    constexpr int WP = SepWork64<N>::WP, H2 = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tws = reinterpret_cast<float2 *>(smem_raw);            // 64 twiddles
+    float2 *work = tws + N;                                          // N rows of WP
+    float2 *slots = work + N * WP;                                   // 16 warps x 256
+    float2 *sl = slots + 16 * 256;                                   // the slice: N rows of WP
+    float2 *ph = sl + N * WP;                                        // phase rows: field a (3 N), field b (3 N)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = lane & 3, t = lane >> 2;
+    float2 *slot = slots + (size_t)warp * 256;
+    const size_t NN = (size_t)N * N;
+    const int ax = blockIdx.x, u = blockIdx.y;
+    const int g0 = (chunk0 + blockIdx.z) * G, ng = min(G, n_groups - g0);
+    if (u >= (sf0 >= 0 ? (sK + 1) / 2 : (ng + 1) / 2 + ng * PPG)) return;   // block-uniform
+    V += (size_t)blockIdx.z * units_per_chunk * 3 * NN;
+    int fa, fb;
+    unit_fields(u, g0, ng, FPG, PPG, prod_local, sf0, sK, fa, fb);
+    {
+        // 16-byte pieces: the slice's 64 rows of 32 pieces, then 2 x 96 phase pieces
+        const float2 *S = nslice + (size_t)ax * NN;
+        for (int i = tid; i < N * N / 2; i += 512) {
+            const int r = i >> 5, q = i & 31;
+            cp_async16(sl + r * WP + 2 * q, S + (size_t)r * N + 2 * q);
+        }
+        if (tid < 3 * N) {
+            const int f = tid < 3 * N / 2 ? fa : (fb >= 0 ? fb : fa), q = tid % (3 * N / 2);
+            cp_async16(ph + (tid < 3 * N / 2 ? 0 : 3 * N) + 2 * q, phase + (size_t)f * 3 * N + 2 * q);
+        }
+        cp_async_commit();
+    }
+    if (tid < N) tws[tid] = tw_g[tid];
+    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+    const float2 *pa = ph, *pb = ph + 3 * N;
+    cp_async_wait<0>();
+    __syncthreads();
+    {
+        const int row = 4 * warp + c, mrow = (N - row) % N;
+        const float2 ca = pa[ax * N + H2], cb = pb[ax * N + H2];
+        const float2 ra = cmul<float>(ca, pa[b0 * N + row]), rma = cmul<float>(ca, pa[b0 * N + mrow]);
+        const float2 rb = cmul<float>(cb, pb[b0 * N + row]), rmb = cmul<float>(cb, pb[b0 * N + mrow]);
+        float2 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int col = t + 8 * e, mcol = (N - col) % N;
+            const float2 s0 = sl[row * WP + col], s1 = sl[mrow * WP + mcol];
+            const float2 ha = herm_half<float>(cmul<float>(s0, cmul<float>(ra, pa[b1 * N + col])),
+                                               cmul<float>(s1, cmul<float>(rma, pa[b1 * N + mcol])));
+            float2 hb = make_float2(0.f, 0.f);
+            if (fb >= 0)
+                hb = herm_half<float>(cmul<float>(s0, cmul<float>(rb, pb[b1 * N + col])),
+                                      cmul<float>(s1, cmul<float>(rmb, pb[b1 * N + mcol])));
+            v[e] = make_float2(ha.x - hb.y, ha.y + hb.x);
+        }
+        line64_swz(v, c, t, slot, tws);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) work[row * WP + t + 8 * e] = v[e];
+    }
+    __syncthreads();
+    {
+        const int z = 4 * warp + c;
+        float2 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = work[(t + 8 * e) * WP + z];
+        line64_swz(v, c, t, slot, tws);
+        float2 *out = V + ((size_t)u * 3 + ax) * NN;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) out[(size_t)(t + 8 * e) * N + z] = v[e];
+    }
+}
+
 // 2D: item = (unit, axis); the slice is a line along the other axis.  One
 // warp per block holds LPW items (one line each).
 template <typename T, int N>

@@ -271,6 +271,17 @@ static int nyquist_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream_
     const cx<T> *ns = static_cast<const cx<T> *>(p.nslice);
     int rc = 0;
     if (hp.d == 3) {
+        if constexpr (N == 64 && sizeof(T) == 4) {       // warp-local lines
+            // twiddles, rows, exchange slots, the staged slice, two fields' phase rows
+            const size_t smem64 = (size_t)(N + 2 * N * SepWork64<N>::WP + 16 * 256 + 6 * N) * sizeof(float2);
+            if ((rc = set_smem(k_nyquist64<N>, smem64))) return rc;
+            k_nyquist64<N><<<dim3(3, upc, nchunks), 512, smem64, s>>>(
+                reinterpret_cast<const float2 *>(ph), reinterpret_cast<float2 *>(V),
+                reinterpret_cast<const float2 *>(tw), reinterpret_cast<const float2 *>(ns), p.prod_local,
+                hp.groups_per_chunk, hp.n_groups, hp.fields_per_group, hp.products_per_group, upc, chunk0, cr.sf0,
+                cr.sK);
+            return (int)cudaGetLastError();
+        }
         if constexpr (N <= 64) {
             const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
             if ((rc = set_smem(k_nyquist_3d<T, N>, smem))) return rc;
