@@ -373,7 +373,9 @@ k_sep_planes_3d(const cx<T> *__restrict__ ghat, const cx<T> *__restrict__ phase,
 // plane (lane = row + 4 t holding j3 = t + 8 e) with line64_swz in its own
 // 256-entry slot and writes them to `work`; after one barrier it transforms
 // 4 consecutive columns (lane = column + 4 t holding j2 = t + 8 e) for every
-// pair of the row value and stores them.  Its planes are column-blocked:
+// pair of the row value and stores them.  The plane of ghat and the phase
+// rows (E2 of the row value, E1 of each of its at most max_value_pairs
+// pairs) are first copied into shared memory with cp.async.  Its planes are column-blocked:
 // point (i2, i3) of a plane at sep_col64(i2 * 64 + i3), blocks of 4 columns
 // one after the other, each 64 rows of 4 points: every store instruction
 // writes 256 contiguous bytes.
@@ -389,28 +391,48 @@ template <int N>
 __global__ void __launch_bounds__(512, 2)
 k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase, float2 *__restrict__ S,
                const float2 *__restrict__ tw_g, const int *__restrict__ sep_v, const int *__restrict__ sep_p, int v0,
-               int p0, int n_fields, int max_pairs) {
+               int p0, int n_fields, int max_pairs, int max_value_pairs) {
     static_assert(N == 64, "64-point lines");
     constexpr int WP = SepWork64<N>::WP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tws = reinterpret_cast<float2 *>(smem_raw);            // 64 twiddles
     float2 *work = tws + N;                                          // N rows of WP
     float2 *slots = work + N * WP;                                   // 16 warps x 256
+    float2 *eph = slots + 16 * 256;                                  // E2 row, then E1 rows of the pairs
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int c = lane & 3, t = lane >> 2;
     const int j1 = blockIdx.x, v = v0 + blockIdx.y;
     const int vf = sep_v[3 * v], pb = sep_v[3 * v + 1], pe = sep_v[3 * v + 2];
-    if (!WKE_GUARD(vf >= 0 && vf < n_fields && pb >= 0 && pb <= pe && pe <= max_pairs, kChkSepPair)) return;
+    if (!WKE_GUARD(vf >= 0 && vf < n_fields && pb >= 0 && pb <= pe && pe <= max_pairs && pe - pb <= max_value_pairs,
+                   kChkSepPair))
+        return;
     float2 *slot = slots + (size_t)warp * 256;
+    {
+        // 16-byte pieces: plane j1 of ghat (64 rows of 32, rows padded to WP in
+        // `work`), then the phase rows (32 pieces each)
+        const int npl = N * N / 2, nph = 32 * (1 + pe - pb);
+        for (int i = tid; i < npl + nph; i += 512) {
+            if (i < npl) {
+                const int r = i >> 5, q = i & 31;
+                cp_async16(work + r * WP + 2 * q, ghat + ((size_t)j1 * N + r) * N + 2 * q);
+            } else {
+                const int k = (i - npl) >> 5, q = (i - npl) & 31;
+                const int f = k == 0 ? vf : sep_p[p0 + pb + k - 1];
+                if (!WKE_GUARD(f >= 0 && f < n_fields, kChkSepPair)) continue;
+                cp_async16(eph + k * N + 2 * q, phase + (size_t)f * 3 * N + (k == 0 ? 2 : 1) * N + 2 * q);
+            }
+        }
+        cp_async_commit();
+    }
     if (tid < N) tws[tid] = tw_g[tid];
-    const float2 *e2 = phase + (size_t)vf * 3 * N + 2 * N;
+    cp_async_wait<0>();
     __syncthreads();
     {
+        // this warp's 4 rows, transformed in place
         const int j2 = 4 * warp + c;
-        const float2 *grow = ghat + ((size_t)j1 * N + j2) * N;
         float2 x[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = cmul<float>(grow[t + 8 * e], e2[t + 8 * e]);
+        for (int e = 0; e < 8; ++e) x[e] = cmul<float>(work[j2 * WP + t + 8 * e], eph[t + 8 * e]);
         line64_swz(x, c, t, slot, tws);
         __syncwarp();
 #pragma unroll
@@ -421,7 +443,7 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
     for (int p = pb; p < pe; ++p) {
         const int pf = sep_p[p0 + p];
         if (!WKE_GUARD(pf >= 0 && pf < n_fields, kChkSepPair)) continue;
-        const float2 *e1 = phase + (size_t)pf * 3 * N + N;
+        const float2 *e1 = eph + (1 + p - pb) * N;
         // column-blocked plane (sep_col64): this warp's 4 columns are one
         // contiguous 64 x 4 block, so each store instruction writes 256 bytes
         float2 *out = S + ((size_t)p * N + j1) * NN + (size_t)warp * 4 * N;

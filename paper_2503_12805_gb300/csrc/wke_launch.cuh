@@ -239,12 +239,14 @@ static int sep_planes_n(const HostPlan &hp, const DevicePtrs &p, int c, cudaStre
         const int v0 = hp.chunk_v0[c], nv = hp.chunk_v0[c + 1] - v0;
         int rc = 0;
         if constexpr (N == 64 && sizeof(T) == 4) {       // warp-local lines
-            const size_t smem64 = (size_t)(N + N * SepWork64<N>::WP + 16 * 256) * sizeof(float2);
+            int mvp = 0;    // most pairs of one row value: the staged E1 rows
+            for (int v = v0; v < v0 + nv; ++v) mvp = std::max(mvp, hp.sep_v[3 * v + 2] - hp.sep_v[3 * v + 1]);
+            const size_t smem64 = (size_t)(N + N * SepWork64<N>::WP + 16 * 256 + (1 + mvp) * N) * sizeof(float2);
             if ((rc = set_smem(k_sep_planes64<N>, smem64))) return rc;
             k_sep_planes64<N><<<dim3(N, nv), 512, smem64, s>>>(
                 static_cast<const float2 *>(p.ghat), static_cast<const float2 *>(p.phase), static_cast<float2 *>(p.S),
                 static_cast<const float2 *>(p.tw), p.sep_v, p.sep_p, v0, hp.chunk_p0[c], hp.n_fields_total,
-                hp.max_chunk_pairs);
+                hp.max_chunk_pairs, mvp);
             return (int)cudaGetLastError();
         }
         const size_t smem = (size_t)(N + N * Work<N>::PITCH + N * LinePad<N>::PITCH) * sizeof(cx<T>);
