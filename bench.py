@@ -196,11 +196,18 @@ def run_gpu(args, rank, world, pool, workers):
 
     # FP32 headline (no per-kernel events in this loop); the launch layout is
     # picked by the library's autotuner before the timed region
-    p32 = make("fp32")
-    info = p32.info()
     f32 = torch.tensor(f64, dtype=torch.float32, device=dev)
     Q32 = torch.empty_like(f32)
-    tuning, tune_ms = p32.autotune(f32, reps=5) if not args.no_autotune else (wke.wke_plan_get_tuning(p32.handle), 0.0)
+    if args.no_autotune:
+        p32 = make("fp32")
+        tune_ms = 0.0
+    else:
+        # pencil layout (separable, shared, per-group) and launch layout both
+        # chosen by timing on this workload
+        p32, tune_ms = wke.Plan.autotuned(f32, w.d, w.N, w.L, w.n_r, w.n_s, w.n_sig, reps=3, sphere=w.sphere,
+                                          precision="fp32", chunk_bytes=int(args.chunk_mb * (1 << 20)))
+    tuning = wke.wke_plan_get_tuning(p32.handle)
+    info = p32.info()
     with ClockSampler(dev.index) as clk:
         ms32, wall32, _ = timed(p32, f32, Q32, args.steps, args.warmup)
     clocks = clk.summary()
@@ -275,7 +282,7 @@ def run_gpu(args, rank, world, pool, workers):
         "tuning": {"pass2_points_per_thread": tuning.pass2_points_per_thread,
                    "pass1_units_per_block": tuning.pass1_units_per_block,
                    "fuse_products": tuning.fuse_products, "rule_products": tuning.rule_products,
-                   "autotune_ms": round(tune_ms, 4)},
+                   "layout": p32.layout or "auto", "autotune_ms": round(tune_ms, 4)},
         "plan": {"groups_per_chunk": info.groups_per_chunk, "n_chunks": info.n_chunks,
                  "separable": info.separable, "fused_products": info.fused_products,
                  "pair_planes_per_eval": info.pair_planes_per_collision, "units_per_eval": info.units_per_collision,

@@ -314,6 +314,28 @@ int wke_plan_set_tuning(wke_plan *plan, const wke_tuning *tuning);
 int wke_plan_autotune(wke_plan *plan, const void *f_dev, void *Q_dev, int reps, wke_tuning *chosen,
                       double *best_ms);
 
+/* Plan creation with the autotuner over pencil layouts as well: the same
+ * evaluation as wke_plan_create (Algorithm 1, Sec. 3.4) for the same
+ * arguments, with the layout chosen by timing.  With quad->layout =
+ * WKE_LAYOUT_AUTO the candidates are WKE_LAYOUT_SEPARABLE (3D, not
+ * WKE_SPLIT), _SHARED and _PER_GROUP (not WKE_SPLIT): which axes every
+ * distinct shifted field is transformed along on its own, and so the
+ * shape of the line batches each transform kernel works on.  A candidate
+ * whose plan cannot be built for this rule (or does not fit in memory) is
+ * skipped; each other one is created, tuned by wke_plan_autotune on f_dev
+ * (device buffer of the plan's grid and precision; Q_dev receives its
+ * results) with `reps` timed evaluations per launch layout on `stream` (NULL:
+ * the plan's own stream), and all but the fastest are destroyed again.  Any
+ * other layout value tunes that layout alone.  *out receives the plan (owned
+ * by the caller, freed with wke_plan_destroy), layout_out (may be NULL) the
+ * layout it uses and best_ms (may be NULL) its milliseconds per evaluation.
+ * Holds at most two plans at a time; synchronises `stream`.  Errors: those of
+ * wke_plan_create when no candidate can be built, else those of
+ * wke_plan_autotune; *out is NULL after an error. */
+int wke_plan_create_autotuned(int d, int N, double L, int M, const wke_quadrature *quad, const void *f_dev,
+                              void *Q_dev, void *stream, int reps, wke_plan **out, int *layout_out,
+                              double *best_ms);
+
 /* Evaluations are captured into a CUDA graph per distinct (f, Q, Qim)
  * pointer set on first use and replayed afterwards (default on; at most 8
  * graphs per plan).  enable = 0 launches every kernel directly instead.  A

@@ -945,6 +945,60 @@ int wke_plan_autotune(wke_plan *plan, const void *f, void *Q, int reps, wke_tuni
     return WKE_OK;
 }
 
+int wke_plan_create_autotuned(int d, int N, double L, int M, const wke_quadrature *quad, const void *f, void *Q,
+                              void *stream, int reps, wke_plan **out, int *layout_out, double *best_ms) {
+    if (!out) return fail(WKE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!quad || !f || !Q || reps < 1) return fail(WKE_ERR_INVALID, "quad, f, Q and reps >= 1 are required");
+    // pencil layouts: which axes each shifted field is transformed along on
+    // its own (per-group and shared: all of them; separable: axis 0 only)
+    std::vector<int> layouts;
+    if (quad->layout != WKE_LAYOUT_AUTO) {
+        layouts.push_back(quad->layout);
+    } else {
+        if (d == 3 && quad->precision != WKE_SPLIT) layouts.push_back(WKE_LAYOUT_SEPARABLE);
+        layouts.push_back(WKE_LAYOUT_SHARED);
+        if (quad->precision != WKE_SPLIT) layouts.push_back(WKE_LAYOUT_PER_GROUP);
+    }
+    wke_plan *best = nullptr;
+    double best_t = 1e300;
+    int best_layout = -1, last_rc = WKE_ERR_INVALID;
+    std::string last_msg = "no layout applies";
+    for (int lay : layouts) {
+        wke_quadrature q = *quad;
+        q.layout = lay;
+        wke_plan *p = nullptr;
+        int rc = wke_plan_create(d, N, L, M, &q, &p);
+        if (rc) {   // this layout does not apply to the rule (or does not fit): try the next
+            last_rc = rc;
+            last_msg = wke_last_error_string();
+            continue;
+        }
+        if (stream) rc = wke_plan_set_stream(p, stream);
+        double ms = 0.0;
+        if (!rc) rc = wke_plan_autotune(p, f, Q, reps, nullptr, &ms);
+        if (rc) {
+            const std::string msg = wke_last_error_string();
+            wke_plan_destroy(p);
+            if (best) wke_plan_destroy(best);
+            return fail(rc, "autotuning layout " + std::to_string(lay) + ": " + msg);
+        }
+        if (ms < best_t) {
+            if (best) wke_plan_destroy(best);
+            best = p;
+            best_t = ms;
+            best_layout = lay;
+        } else {
+            wke_plan_destroy(p);
+        }
+    }
+    if (!best) return fail(last_rc, last_msg);
+    *out = best;
+    if (layout_out) *layout_out = best_layout;
+    if (best_ms) *best_ms = best_t;
+    return WKE_OK;
+}
+
 int wke_plan_use_graphs(wke_plan *plan, int enable) {
     if (!plan) return fail(WKE_ERR_INVALID, "plan is NULL");
     plan->use_graphs = enable != 0;

@@ -1501,14 +1501,16 @@ k_fused_3d(const cx<T> *__restrict__ src, const cx<T> *__restrict__ phase, const
 }
 
 // Fused axis-0 transform and product pass for N = 64 in FP32.  A block holds
-// 4 consecutive columns of one i2 row (256 points, 256 threads) and one field
-// slot of 256 points per field.  It first copies with cp.async its columns of
-// the chunk's pair planes (separable plans) or of the pass-1 units into
-// shared memory, then each warp transforms whole units: the axis-0 input
-// from the staged columns (and, separable, the fields' axis-0 phases), the
-// line transform with the exchange of line64_swz in the unit's first slot,
-// and the unpacking into the unit's two slots with the Nyquist imaginary
-// parts, whose table entries the warp loads from L2 before the transform.
+// 4 consecutive columns of one i2 row (256 points, 256 threads) and one slot
+// of 256 points per unit, its two fields interleaved (16 bytes per point).
+// It first copies with cp.async its columns of the chunk's pair planes
+// (separable plans) or of the pass-1 units into shared memory, then each
+// warp transforms whole units: the axis-0 input from the staged columns
+// (and, separable, the fields' axis-0 phases), the line transform with the
+// exchange of line64_swz in the first half of the unit's slot, and the
+// unpacking of both fields into the slot (one 16-byte store per point) with
+// the Nyquist imaginary parts, whose table entries the warp loads from L2
+// before the transform.
 // After one barrier every thread forms the products at its point with the
 // algebra and summation order of k_fused_3d.  The chunk's product schedule
 // arrives as a kernel parameter with shared-memory byte offsets, so that
@@ -1522,7 +1524,8 @@ constexpr int kF64Pts = 256;
 
 struct Fused64Tab {
     static constexpr int kMaxProducts = 256, kMaxGroups = 64, kMaxUnits = 128;
-    unsigned oa[kMaxProducts], ob[kMaxProducts];   // byte offsets of each product's fields
+    unsigned oa[kMaxProducts], ob[kMaxProducts];   // byte offsets of each product's fields from the
+                                                   // point's unit entry: (l / 2) 256 * 16 + (l % 2) 8
     unsigned oc[kMaxGroups];                       // byte offset of each group's C field
     float w[kMaxProducts];
     unsigned char pla[kMaxUnits], plb[kMaxUnits];  // separable plans: pair plane of each unit's fields
@@ -1538,10 +1541,11 @@ __device__ __forceinline__ void pu_acc(float2 &P, float2 &U, float2 A, float2 B)
 }
 
 // CUBE: the cube rule's schedule (3 products per group, 8 groups, one weight
-// per group).  tab.oa[2 i + s] is the edge field of axis i (s = 1: negative),
-// tab.ob[4 i + q] the face field with component i zero (q's bit 0: the lower
-// other axis negative, bit 1: the higher one), tab.oc[v] and tab.w[v] the C
-// field and weight of the group of vertex v (bit a: v_a < 0).
+// per group) on a chunk whose 26 fields the plan ordered as the edge fields
+// (field 2 i + s: axis i, s = 1 negative), the face fields (6 + 4 i + q: the
+// face with component i zero, q's bit 0 the lower other axis negative, bit 1
+// the higher one) and the C fields (18 + v: the group of vertex v, bit a:
+// v_a < 0); tab.w[v] is the weight of the group of vertex v.
 template <bool SEP, bool IM, bool NYQ, int PPGC, int NGC, bool EQW, bool CUBE>
 __global__ void __launch_bounds__(256, 3)
 k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const float2 *__restrict__ Vtab,
@@ -1552,14 +1556,16 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
     constexpr int N = 64, CB = 4, PTS = kF64Pts, P = N * N;
     constexpr size_t ND = (size_t)N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *fld = reinterpret_cast<float2 *>(smem_raw);             // K slots of PTS points
-    float2 *pst = fld + (size_t)K * PTS;                              // staged planes: [plane][j1][c]
+    const int U = (K + 1) / 2;
+    // unit u's two fields interleaved: field 2u + h of point pt at float2
+    // index (u PTS + pt) 2 + h, so that one 16-byte access covers both
+    float2 *fld = reinterpret_cast<float2 *>(smem_raw);             // U unit slots of PTS points
+    float2 *pst = fld + (size_t)2 * U * PTS;                          // staged planes: [plane][j1][c]
     float2 *tws = pst + (size_t)nplanes * PTS;                        // twiddles exp(2 pi i k / 64)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int c = lane & 3, t = lane >> 2;
     const int col0 = blockIdx.x * CB;
     const int i2 = col0 >> 6, i30 = col0 & 63;
-    const int U = (K + 1) / 2;
     // ---- stage the planes: 128 pieces of 16 bytes per plane, two planes per pass
     {
         const int j1 = (tid >> 1) & 63, h = tid & 1;
@@ -1618,17 +1624,19 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
                 a = sgn1 * v0.x + s2 * vr[e].x + s3 * vr[8 + e].x;
                 b = sgn1 * v0.y + s2 * vr[e].y + s3 * vr[8 + e].y;
             }
-            slot[pt] = make_float2(v[e].x + b, a);
-            if (pair) slot[PTS + pt] = make_float2(v[e].y - a, b);
+            if (pair)
+                *reinterpret_cast<float4 *>(slot + 2 * pt) = make_float4(v[e].x + b, a, v[e].y - a, b);
+            else
+                slot[2 * pt] = make_float2(v[e].x + b, a);
         }
     }
     __syncthreads();
     // ---- products at this thread's point
     const int pt = tid;
     const size_t idx = (size_t)(pt >> 2) * P + col0 + (pt & 3);
-    const unsigned char *fb = reinterpret_cast<const unsigned char *>(fld + pt);
-    // checked builds: a schedule offset outside the K field slots reads slot 0
-    const unsigned olim = (unsigned)K * PTS * sizeof(float2);
+    const unsigned char *fb = reinterpret_cast<const unsigned char *>(fld + 2 * pt);
+    // checked builds: a schedule offset outside the U unit slots reads slot 0
+    const unsigned olim = (unsigned)U * PTS * sizeof(float4);
     auto off = [&](unsigned o) -> unsigned { return WKE_GUARD(o < olim, kChkFusedSchedule) ? o : 0u; };
     const float F = f[idx];
     const int ppg = PPGC > 0 ? PPGC : PPG;
@@ -1638,26 +1646,41 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
         // axis by axis: the two edge fields of axis i meet its four face
         // fields, each pair a product of the vertex they agree with, so that
         // every field is read once per point; P = sum A B and U = sum (A + B)
-        // per group in registers
+        // per group in registers.  The plan orders the chunk's fields so that
+        // unit i holds the edges of axis i (+, -), units 3 + 2i and 4 + 2i its
+        // faces (q = 0, 1 and 2, 3) and units 9 + v/2 the C fields of the
+        // vertices, so each load takes the two fields of one unit.
+        constexpr unsigned kUnit = PTS * sizeof(float4);
+        const bool ok = WKE_GUARD(K == 26, kChkFusedSchedule);
+        auto unit2 = [&](int u) -> float4 {
+            return ok ? *reinterpret_cast<const float4 *>(fb + u * kUnit) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
         float2 Pq[8], Uq[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) Pq[v] = Uq[v] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
-            const float2 Ep = *reinterpret_cast<const float2 *>(fb + off(tab.oa[2 * i]));
-            const float2 Em = *reinterpret_cast<const float2 *>(fb + off(tab.oa[2 * i + 1]));
+            const float4 E2 = unit2(i);
+            const float2 Ep = make_float2(E2.x, E2.y), Em = make_float2(E2.z, E2.w);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 Fc = *reinterpret_cast<const float2 *>(fb + off(tab.ob[4 * i + q]));
-                const int vp = ((q & 1) << j) | ((q >> 1) << k), vm = vp | (1 << i);
-                pu_acc(Pq[vp], Uq[vp], Ep, Fc);
-                pu_acc(Pq[vm], Uq[vm], Em, Fc);
+            for (int h = 0; h < 2; ++h) {
+                const float4 F2 = unit2(3 + 2 * i + h);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = 2 * h + r;
+                    const float2 Fc = r ? make_float2(F2.z, F2.w) : make_float2(F2.x, F2.y);
+                    const int vp = ((q & 1) << j) | ((q >> 1) << k), vm = vp | (1 << i);
+                    pu_acc(Pq[vp], Uq[vp], Ep, Fc);
+                    pu_acc(Pq[vm], Uq[vm], Em, Fc);
+                }
             }
         }
+        float4 C2 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const float2 C = *reinterpret_cast<const float2 *>(fb + off(tab.oc[v]));
+            if ((v & 1) == 0) C2 = unit2(9 + v / 2);
+            const float2 C = (v & 1) ? make_float2(C2.z, C2.w) : make_float2(C2.x, C2.y);
             const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
             const float w = tab.w[v];
             const float acc = w * ((sr * Pq[v].x - si * Pq[v].y) - (cr * Uq[v].x - ci * Uq[v].y));

@@ -375,15 +375,18 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
         // field slots, staged planes and twiddles, when they fit
         const int U = (cr.sK + 1) / 2;
         const int nplanes = SEP ? hp.chunk_p0[c + 1] - hp.chunk_p0[c] : U;
-        const size_t smem64 = ((size_t)(cr.sK + nplanes) * kF64Pts + N) * sizeof(float2);
+        const size_t smem64 = ((size_t)(2 * U + nplanes) * kF64Pts + N) * sizeof(float2);
         if (smem64 <= kMaxDynamicSmem && U <= Fused64Tab::kMaxUnits) {
             Fused64Tab t64;
+            // byte offset of a chunk-local field from its point's unit entry:
+            // the two fields of unit u are interleaved (k_fused64)
+            auto foff = [](int l) { return (unsigned)((l >> 1) * kF64Pts * sizeof(float4) + (l & 1) * sizeof(float2)); };
             for (int i = 0; i < np; ++i) {
-                t64.oa[i] = (unsigned)tab.pa[i] * kF64Pts * sizeof(float2);
-                t64.ob[i] = (unsigned)tab.pb[i] * kF64Pts * sizeof(float2);
+                t64.oa[i] = foff(tab.pa[i]);
+                t64.ob[i] = foff(tab.pb[i]);
                 t64.w[i] = (float)tab.w[i];
             }
-            for (int g = 0; g < cr.ng; ++g) t64.oc[g] = (unsigned)tab.cf[g] * kF64Pts * sizeof(float2);
+            for (int g = 0; g < cr.ng; ++g) t64.oc[g] = foff(tab.cf[g]);
             if (SEP)
                 for (int u = 0; u < U; ++u) {
                     const int fa = cr.sf0 + 2 * u, fb = 2 * u + 1 < cr.sK ? fa + 1 : fa;
@@ -406,16 +409,16 @@ static int fused_nimp(const HostPlan &hp, const DevicePtrs &p, int c, cudaStream
             static_cast<float *>(p.Qout), static_cast<float *>(p.Qiout), p.scale_out);                          \
     } while (0)
             if constexpr (PPGC == 3) {
-                if (!hp.cube.empty() && hp.tune_rule_products) {
+                const HostPlan::CubeChunk *cu = hp.cube.empty() ? nullptr : &hp.cube[c];
+                // the kernel reads the fields in the order the plan gives them
+                // (edges, faces, C fields; wke_plan.cpp, order_cube_fields)
+                bool canonical = cu != nullptr && cr.sK == 26;
+                for (int i = 0; i < 6 && canonical; ++i) canonical = cu->edge[i] == i;
+                for (int i = 0; i < 12 && canonical; ++i) canonical = cu->face[i] == 6 + i;
+                for (int v = 0; v < 8 && canonical; ++v) canonical = cu->cfield[v] == 18 + v;
+                if (canonical && hp.tune_rule_products) {
                     // the cube rule's schedule: every field read once per point
-                    const HostPlan::CubeChunk &cu = hp.cube[c];
-                    const unsigned sb = kF64Pts * sizeof(float2);
-                    for (int i = 0; i < 6; ++i) t64.oa[i] = (unsigned)cu.edge[i] * sb;
-                    for (int i = 0; i < 12; ++i) t64.ob[i] = (unsigned)cu.face[i] * sb;
-                    for (int v = 0; v < 8; ++v) {
-                        t64.oc[v] = (unsigned)cu.cfield[v] * sb;
-                        t64.w[v] = (float)cu.w[v];
-                    }
+                    for (int v = 0; v < 8; ++v) t64.w[v] = (float)cu->w[v];
                     WKE_F64_LAUNCH(8, true, true);
                     return (int)cudaGetLastError();
                 }

@@ -322,83 +322,119 @@ static int build_shared_layout(HostPlan &hp, bool force) {
 // matches when its C field is a vertex v, its three products are each one
 // edge and one face field of v for distinct axes, and the three weights are
 // equal.
+static bool classify_cube_chunk(const HostPlan &hp, int c, HostPlan::CubeChunk &t) {
+    const int g0 = hp.chunk_g0[c], g1 = hp.chunk_g0[c + 1], f0 = hp.chunk_f0[c], K = hp.chunk_f0[c + 1] - f0;
+    if (g1 - g0 != 8 || K != 26) return false;
+    double m = 0.0;
+    for (int l = 0; l < K; ++l)
+        for (int a = 0; a < 3; ++a) m = std::max(m, std::fabs(hp.field_shift[(size_t)(f0 + l) * 3 + a]));
+    if (!(m > 0.0)) return false;
+    std::vector<int> sg(3 * K), nz(K, 0);
+    for (int l = 0; l < K; ++l)
+        for (int a = 0; a < 3; ++a) {
+            const double x = hp.field_shift[(size_t)(f0 + l) * 3 + a] / m;
+            if (std::fabs(x) <= 1e-9) sg[3 * l + a] = 0;
+            else if (std::fabs(x - 1.0) <= 1e-9) sg[3 * l + a] = 1;
+            else if (std::fabs(x + 1.0) <= 1e-9) sg[3 * l + a] = -1;
+            else return false;
+            nz[l] += sg[3 * l + a] != 0;
+        }
+    std::fill(std::begin(t.edge), std::end(t.edge), -1);
+    std::fill(std::begin(t.face), std::end(t.face), -1);
+    std::fill(std::begin(t.cfield), std::end(t.cfield), -1);
+    auto zero_axis = [&](int l) {
+        for (int a = 0; a < 3; ++a)
+            if (sg[3 * l + a] == 0) return a;
+        return -1;
+    };
+    auto nonzero_axis = [&](int l) {
+        for (int a = 0; a < 3; ++a)
+            if (sg[3 * l + a] != 0) return a;
+        return -1;
+    };
+    for (int l = 0; l < K; ++l) {
+        if (nz[l] == 1) {
+            const int i = nonzero_axis(l);
+            int &e = t.edge[2 * i + (sg[3 * l + i] < 0)];
+            if (e >= 0) return false;
+            e = l;
+        } else if (nz[l] == 2) {
+            const int i = zero_axis(l), j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
+            int &f = t.face[4 * i + (sg[3 * l + j] < 0) + 2 * (sg[3 * l + k] < 0)];
+            if (f >= 0) return false;
+            f = l;
+        }
+    }
+    for (int g = g0; g < g1; ++g) {
+        const int cf = hp.group_cfield[g];
+        if (nz[cf] != 3) return false;
+        const int v = (sg[3 * cf] < 0) + 2 * (sg[3 * cf + 1] < 0) + 4 * (sg[3 * cf + 2] < 0);
+        if (t.cfield[v] >= 0) return false;
+        t.cfield[v] = cf;
+        t.w[v] = hp.prod_W[(size_t)g * 3];
+        int axes = 0;
+        for (int q = 0; q < 3; ++q) {
+            const size_t slot = (size_t)g * 3 + q;
+            if (hp.prod_W[slot] != t.w[v]) return false;
+            int fe = hp.prod_fa[slot], ff = hp.prod_fb[slot];
+            if (nz[fe] == 2) std::swap(fe, ff);
+            if (nz[fe] != 1 || nz[ff] != 2) return false;
+            const int i = nonzero_axis(fe);
+            if (zero_axis(ff) != i || (axes >> i) & 1) return false;
+            axes |= 1 << i;
+            for (int a = 0; a < 3; ++a)
+                if ((a == i ? sg[3 * fe + a] : sg[3 * ff + a]) != sg[3 * cf + a]) return false;
+        }
+    }
+    for (int i = 0; i < 6; ++i)
+        if (t.edge[i] < 0) return false;
+    for (int i = 0; i < 12; ++i)
+        if (t.face[i] < 0) return false;
+    for (int i = 0; i < 8; ++i)
+        if (t.cfield[i] < 0) return false;
+    return true;
+}
+
 static void build_cube_schedule(HostPlan &hp) {
     hp.cube.clear();
     if (!(hp.shared && hp.d == 3 && hp.N == 64 && hp.products_per_group == 3)) return;   // k_fused64's schedule
     std::vector<HostPlan::CubeChunk> tabs(hp.n_chunks);
+    for (int c = 0; c < hp.n_chunks; ++c)
+        if (!classify_cube_chunk(hp, c, tabs[c])) return;
+    hp.cube = tabs;
+}
+
+// Order the fields of every chunk of the cube rule's form as the fused
+// kernel reads them: the edge fields (index 2 i + [sign < 0]), then the face
+// fields (index 4 i + q), then the C fields by vertex, so that the two
+// fields of each unit (fields 2u, 2u + 1) are read together in the product
+// phase: edges +-e_i, two faces of the same axis, the C fields of two
+// vertices.  A renaming of the chunk's field ids (shifts, products and C
+// fields follow it); the evaluation is the same up to rounding.
+static void order_cube_fields(HostPlan &hp) {
+    if (!(hp.shared && hp.d == 3 && hp.N == 64 && hp.products_per_group == 3)) return;
+    std::vector<HostPlan::CubeChunk> tabs(hp.n_chunks);
+    for (int c = 0; c < hp.n_chunks; ++c)
+        if (!classify_cube_chunk(hp, c, tabs[c])) return;
     for (int c = 0; c < hp.n_chunks; ++c) {
-        const int g0 = hp.chunk_g0[c], g1 = hp.chunk_g0[c + 1], f0 = hp.chunk_f0[c], K = hp.chunk_f0[c + 1] - f0;
-        if (g1 - g0 != 8 || K != 26) return;
-        double m = 0.0;
-        for (int l = 0; l < K; ++l)
-            for (int a = 0; a < 3; ++a) m = std::max(m, std::fabs(hp.field_shift[(size_t)(f0 + l) * 3 + a]));
-        if (!(m > 0.0)) return;
-        std::vector<int> sg(3 * K), nz(K, 0);
-        for (int l = 0; l < K; ++l)
-            for (int a = 0; a < 3; ++a) {
-                const double x = hp.field_shift[(size_t)(f0 + l) * 3 + a] / m;
-                if (std::fabs(x) <= 1e-9) sg[3 * l + a] = 0;
-                else if (std::fabs(x - 1.0) <= 1e-9) sg[3 * l + a] = 1;
-                else if (std::fabs(x + 1.0) <= 1e-9) sg[3 * l + a] = -1;
-                else return;
-                nz[l] += sg[3 * l + a] != 0;
-            }
-        HostPlan::CubeChunk &t = tabs[c];
-        std::fill(std::begin(t.edge), std::end(t.edge), -1);
-        std::fill(std::begin(t.face), std::end(t.face), -1);
-        std::fill(std::begin(t.cfield), std::end(t.cfield), -1);
-        auto zero_axis = [&](int l) {
-            for (int a = 0; a < 3; ++a)
-                if (sg[3 * l + a] == 0) return a;
-            return -1;
-        };
-        auto nonzero_axis = [&](int l) {
-            for (int a = 0; a < 3; ++a)
-                if (sg[3 * l + a] != 0) return a;
-            return -1;
-        };
-        for (int l = 0; l < K; ++l) {
-            if (nz[l] == 1) {
-                const int i = nonzero_axis(l);
-                int &e = t.edge[2 * i + (sg[3 * l + i] < 0)];
-                if (e >= 0) return;
-                e = l;
-            } else if (nz[l] == 2) {
-                const int i = zero_axis(l), j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
-                int &f = t.face[4 * i + (sg[3 * l + j] < 0) + 2 * (sg[3 * l + k] < 0)];
-                if (f >= 0) return;
-                f = l;
-            }
-        }
-        for (int g = g0; g < g1; ++g) {
-            const int cf = hp.group_cfield[g];
-            if (nz[cf] != 3) return;
-            const int v = (sg[3 * cf] < 0) + 2 * (sg[3 * cf + 1] < 0) + 4 * (sg[3 * cf + 2] < 0);
-            if (t.cfield[v] >= 0) return;
-            t.cfield[v] = cf;
-            t.w[v] = hp.prod_W[(size_t)g * 3];
-            int axes = 0;
+        const HostPlan::CubeChunk &t = tabs[c];
+        const int f0 = hp.chunk_f0[c];
+        int perm[26];    // old chunk-local id -> new
+        for (int k = 0; k < 6; ++k) perm[t.edge[k]] = k;
+        for (int k = 0; k < 12; ++k) perm[t.face[k]] = 6 + k;
+        for (int v = 0; v < 8; ++v) perm[t.cfield[v]] = 18 + v;
+        std::vector<double> sh(hp.field_shift.begin() + (size_t)f0 * 3, hp.field_shift.begin() + (size_t)(f0 + 26) * 3);
+        for (int l = 0; l < 26; ++l)
+            for (int a = 0; a < 3; ++a) hp.field_shift[(size_t)(f0 + perm[l]) * 3 + a] = sh[(size_t)l * 3 + a];
+        for (int g = hp.chunk_g0[c]; g < hp.chunk_g0[c + 1]; ++g) {
+            hp.group_cfield[g] = perm[hp.group_cfield[g]];
             for (int q = 0; q < 3; ++q) {
                 const size_t slot = (size_t)g * 3 + q;
-                if (hp.prod_W[slot] != t.w[v]) return;
-                int fe = hp.prod_fa[slot], ff = hp.prod_fb[slot];
-                if (nz[fe] == 2) std::swap(fe, ff);
-                if (nz[fe] != 1 || nz[ff] != 2) return;
-                const int i = nonzero_axis(fe);
-                if (zero_axis(ff) != i || (axes >> i) & 1) return;
-                axes |= 1 << i;
-                for (int a = 0; a < 3; ++a)
-                    if ((a == i ? sg[3 * fe + a] : sg[3 * ff + a]) != sg[3 * cf + a]) return;
+                hp.prod_fa[slot] = perm[hp.prod_fa[slot]];
+                hp.prod_fb[slot] = perm[hp.prod_fb[slot]];
             }
         }
-        for (int i = 0; i < 6; ++i)
-            if (t.edge[i] < 0) return;
-        for (int i = 0; i < 12; ++i)
-            if (t.face[i] < 0) return;
-        for (int i = 0; i < 8; ++i)
-            if (t.cfield[i] < 0) return;
     }
-    hp.cube = tabs;
 }
 
 // Separable transforms (3D, shared-field layout; see HostPlan::separable).
@@ -701,6 +737,7 @@ int build_host_plan(int d, int N, double L, int M, const wke_quadrature *quad, H
     }
     if (hp.split && (d != 3 || (hp.N != 32 && hp.N != 64)))
         return fail(WKE_ERR_UNSUPPORTED, "WKE_SPLIT is built for 3D transform grids of N = 32 or 64");
+    if (hp.shared && d == 3 && hp.precision == WKE_FP32 && !hp.split) order_cube_fields(hp);
     if (hp.shared && d == 3 && !hp.split && quad->layout != WKE_LAYOUT_SHARED) {
         int rc2 = build_separable(hp, quad->layout == WKE_LAYOUT_SEPARABLE);
         if (rc2) return rc2;

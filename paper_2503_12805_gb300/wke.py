@@ -93,6 +93,7 @@ EXPORTED = [
     "wke_collision_host", "wke_collision_spectrum", "wke_plan_set_stream", "wke_step", "wke_moments",
     "wke_server_create", "wke_server_submit", "wke_server_cancel", "wke_server_wait", "wke_server_destroy",
     "wke_moments_noalloc", "wke_plan_get_tuning", "wke_plan_set_tuning", "wke_plan_autotune",
+    "wke_plan_create_autotuned",
     "wke_plan_use_graphs", "wke_plan_profile", "wke_plan_profile_read", "wke_alu_peak", "wke_check_status",
     "wke_last_error_string", "wke_version",
 ]
@@ -130,6 +131,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "wke_plan_get_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
         "wke_plan_set_tuning": (i, [vp, ctypes.POINTER(WkeTuning)]),
         "wke_plan_autotune": (i, [vp, vp, vp, i, ctypes.POINTER(WkeTuning), ctypes.POINTER(ctypes.c_double)]),
+        "wke_plan_create_autotuned": (i, [i, i, d, i, QP, vp, vp, vp, i, ctypes.POINTER(vp), ctypes.POINTER(i),
+                                          ctypes.POINTER(ctypes.c_double)]),
         "wke_plan_use_graphs": (i, [vp, i]),
         "wke_plan_profile": (i, [vp, i]),
         "wke_plan_profile_read": (i, [vp, C_DOUBLE_P]),
@@ -271,6 +274,18 @@ def wke_plan_autotune(plan, f_ptr: int, Q_ptr: int, reps: int = 5):
     return t, ms.value
 
 
+def wke_plan_create_autotuned(d: int, N: int, L: float, M: int, quad: WkeQuadrature, f_ptr: int, Q_ptr: int,
+                              stream: int | None = None, reps: int = 3):
+    """Create the plan whose pencil and launch layouts time fastest on f;
+    returns (plan handle, layout, ms per evaluation)."""
+    out = ctypes.c_void_p()
+    lay = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib().wke_plan_create_autotuned(d, N, L, M, ctypes.byref(quad), f_ptr, Q_ptr, stream, reps,
+                                           ctypes.byref(out), ctypes.byref(lay), ctypes.byref(ms)))
+    return out, lay.value, ms.value
+
+
 def wke_plan_use_graphs(plan, enable: bool) -> None:
     _check(lib().wke_plan_use_graphs(plan, int(enable)))
 
@@ -400,6 +415,42 @@ def _rule(name: str | None):
     return SPHERE_NAMES[name], 0
 
 
+LAYOUT_NAMES = {"auto": WKE_LAYOUT_AUTO, "per_group": WKE_LAYOUT_PER_GROUP, "shared": WKE_LAYOUT_SHARED,
+                "separable": WKE_LAYOUT_SEPARABLE}
+
+
+def _quadrature(n_r, n_s, n_sig, sphere, sphere_sig, R, precision, nyquist, pair_antipodal, chunk_bytes,
+                dispersion, user_s, user_sig, dealias, layout):
+    """The wke_quadrature descriptor of Plan's keywords, and the arrays its
+    user rules point into (to be kept alive with it)."""
+    import numpy as np
+    q = wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = n_r, n_s, n_sig
+    q.sphere_rule, q.sphere_param = _rule(sphere)
+    if sphere_sig is not None:
+        q.sphere_rule_sig, q.sphere_param_sig = _rule(sphere_sig)
+    keep = []
+    if user_s is not None:
+        arr = np.ascontiguousarray(user_s, dtype=np.float64)
+        keep.append(arr)
+        q.sphere_rule = WKE_SPHERE_USER
+        q.user_s = arr.ctypes.data_as(C_DOUBLE_P)
+    if user_sig is not None:
+        arr = np.ascontiguousarray(user_sig, dtype=np.float64)
+        keep.append(arr)
+        q.sphere_rule_sig = WKE_SPHERE_USER
+        q.user_sig = arr.ctypes.data_as(C_DOUBLE_P)
+    q.R = R
+    q.precision = {"fp64": WKE_FP64, "fp32": WKE_FP32, "split": WKE_SPLIT}[precision]
+    q.nyquist = {"keep": WKE_NYQ_KEEP, "zero": WKE_NYQ_ZERO}[nyquist]
+    q.dispersion = {"half_k2": WKE_OMEGA_HALF_K2, "k2": WKE_OMEGA_K2}[dispersion]
+    q.pair_antipodal = int(pair_antipodal)
+    q.chunk_bytes = chunk_bytes
+    q.alias = WKE_DEALIAS_PAD2 if dealias else WKE_ALIAS_CIRCULAR
+    q.layout = LAYOUT_NAMES[layout]
+    return q, keep
+
+
 class Plan:
     """A plan on the current CUDA device; tensors are torch CUDA tensors."""
 
@@ -407,38 +458,38 @@ class Plan:
                  sphere: str | None = None, sphere_sig: str | None = None, R: float = 0.0,
                  precision: str = "fp64", nyquist: str = "keep", pair_antipodal: bool = True,
                  chunk_bytes: int = 0, dispersion: str = "half_k2", user_s=None, user_sig=None,
-                 dealias: bool = False, layout: str = "auto"):
-        import numpy as np
-        q = wke_quadrature_default()
-        q.n_r, q.n_s, q.n_sig = n_r, n_s, n_sig
-        q.sphere_rule, q.sphere_param = _rule(sphere)
-        if sphere_sig is not None:
-            q.sphere_rule_sig, q.sphere_param_sig = _rule(sphere_sig)
-        self._keep = []
-        if user_s is not None:
-            arr = np.ascontiguousarray(user_s, dtype=np.float64)
-            self._keep.append(arr)
-            q.sphere_rule = WKE_SPHERE_USER
-            q.user_s = arr.ctypes.data_as(C_DOUBLE_P)
-        if user_sig is not None:
-            arr = np.ascontiguousarray(user_sig, dtype=np.float64)
-            self._keep.append(arr)
-            q.sphere_rule_sig = WKE_SPHERE_USER
-            q.user_sig = arr.ctypes.data_as(C_DOUBLE_P)
-        q.R = R
-        q.precision = {"fp64": WKE_FP64, "fp32": WKE_FP32, "split": WKE_SPLIT}[precision]
-        q.nyquist = {"keep": WKE_NYQ_KEEP, "zero": WKE_NYQ_ZERO}[nyquist]
-        q.dispersion = {"half_k2": WKE_OMEGA_HALF_K2, "k2": WKE_OMEGA_K2}[dispersion]
-        q.pair_antipodal = int(pair_antipodal)
-        q.chunk_bytes = chunk_bytes
-        q.alias = WKE_DEALIAS_PAD2 if dealias else WKE_ALIAS_CIRCULAR
-        q.layout = {"auto": WKE_LAYOUT_AUTO, "per_group": WKE_LAYOUT_PER_GROUP, "shared": WKE_LAYOUT_SHARED,
-                    "separable": WKE_LAYOUT_SEPARABLE}[layout]
+                 dealias: bool = False, layout: str = "auto", _handle=None):
+        q, self._keep = _quadrature(n_r, n_s, n_sig, sphere, sphere_sig, R, precision, nyquist, pair_antipodal,
+                                    chunk_bytes, dispersion, user_s, user_sig, dealias, layout)
         self.d, self.N, self.L = d, N, L
         self.M = n_r * n_s * n_sig
         self.precision = precision
         self.quad = q                      # the descriptor (its user rules are kept alive above)
-        self.handle = wke_plan_create(d, N, L, self.M, q)
+        self.layout = None                 # set by Plan.autotuned
+        self.handle = wke_plan_create(d, N, L, self.M, q) if _handle is None else _handle
+
+    @classmethod
+    def autotuned(cls, f, d: int, N: int, L: float, n_r: int, n_s: int, n_sig: int, reps: int = 3, **kw):
+        """The plan whose pencil layout (separable, shared or per-group) and
+        launch layout time fastest on f (a CUDA tensor of the plan's grid
+        and precision), through wke_plan_create_autotuned; the keywords are
+        those of Plan.  Returns (plan, ms per evaluation)."""
+        import torch
+        prec = kw.get("precision", "fp64")
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        if not (f.is_cuda and f.dtype == dt and f.is_contiguous() and tuple(f.shape) == (N,) * d):
+            raise ValueError(f"expected a contiguous CUDA {dt} tensor of shape {(N,) * d}")
+        q, keep = _quadrature(n_r, n_s, n_sig, kw.get("sphere"), kw.get("sphere_sig"), kw.get("R", 0.0), prec,
+                              kw.get("nyquist", "keep"), kw.get("pair_antipodal", True), kw.get("chunk_bytes", 0),
+                              kw.get("dispersion", "half_k2"), kw.get("user_s"), kw.get("user_sig"),
+                              kw.get("dealias", False), kw.get("layout", "auto"))
+        Q = torch.empty_like(f)
+        h, lay, ms = wke_plan_create_autotuned(d, N, L, n_r * n_s * n_sig, q, f.data_ptr(), Q.data_ptr(),
+                                               torch.cuda.current_stream().cuda_stream, reps)
+        plan = cls(d, N, L, n_r, n_s, n_sig, _handle=h, **kw)
+        plan._keep += keep
+        plan.layout = {v: k for k, v in LAYOUT_NAMES.items()}[lay]
+        return plan, ms
 
     @property
     def dtype(self):
