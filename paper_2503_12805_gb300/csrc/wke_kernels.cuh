@@ -1655,9 +1655,8 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
         auto unit2 = [&](int u) -> float4 {
             return ok ? *reinterpret_cast<const float4 *>(fb + u * kUnit) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
+        // (axis 0 sets every vertex's P and U, axes 1 and 2 add to them)
         float2 Pq[8], Uq[8];
-#pragma unroll
-        for (int v = 0; v < 8; ++v) Pq[v] = Uq[v] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int j = i == 0 ? 1 : 0, k = i == 2 ? 1 : 2;
@@ -1671,26 +1670,42 @@ k_fused64(const float2 *__restrict__ src, const float4 *__restrict__ ue0, const 
                     const int q = 2 * h + r;
                     const float2 Fc = r ? make_float2(F2.z, F2.w) : make_float2(F2.x, F2.y);
                     const int vp = ((q & 1) << j) | ((q >> 1) << k), vm = vp | (1 << i);
-                    pu_acc(Pq[vp], Uq[vp], Ep, Fc);
-                    pu_acc(Pq[vm], Uq[vm], Em, Fc);
+                    if (i == 0) {
+                        Pq[vp] = cmul<float>(Ep, Fc);
+                        Uq[vp] = cadd<float>(Ep, Fc);
+                        Pq[vm] = cmul<float>(Em, Fc);
+                        Uq[vm] = cadd<float>(Em, Fc);
+                    } else {
+                        pu_acc(Pq[vp], Uq[vp], Ep, Fc);
+                        pu_acc(Pq[vm], Uq[vm], Em, Fc);
+                    }
                 }
             }
         }
-        float4 C2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        // the groups of vertices 2n and 2n + 1 (one C-field unit) are added
+        // plainly and their sum enters the compensated running sum
+        float pr = 0.f, pri = 0.f;
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            if ((v & 1) == 0) C2 = unit2(9 + v / 2);
+            const float4 C2 = unit2(9 + v / 2);
             const float2 C = (v & 1) ? make_float2(C2.z, C2.w) : make_float2(C2.x, C2.y);
             const float sr = C.x + F, si = C.y, cr = C.x * F, ci = C.y * F;
             const float w = tab.w[v];
             const float acc = w * ((sr * Pq[v].x - si * Pq[v].y) - (cr * Uq[v].x - ci * Uq[v].y));
-            float tsum = sum + acc;
-            comp += fabsf(sum) >= fabsf(acc) ? (sum - tsum) + acc : (acc - tsum) + sum;
+            const float acci = IM ? w * ((sr * Pq[v].y + si * Pq[v].x) - (cr * Uq[v].y + ci * Uq[v].x)) : 0.f;
+            if ((v & 1) == 0) {
+                pr = acc;
+                pri = acci;
+                continue;
+            }
+            const float a = pr + acc;
+            float tsum = sum + a;
+            comp += fabsf(sum) >= fabsf(a) ? (sum - tsum) + a : (a - tsum) + sum;
             sum = tsum;
             if (IM) {
-                const float acci = w * ((sr * Pq[v].y + si * Pq[v].x) - (cr * Uq[v].y + ci * Uq[v].x));
-                tsum = sumi + acci;
-                compi += fabsf(sumi) >= fabsf(acci) ? (sumi - tsum) + acci : (acci - tsum) + sumi;
+                const float ai = pri + acci;
+                tsum = sumi + ai;
+                compi += fabsf(sumi) >= fabsf(ai) ? (sumi - tsum) + ai : (ai - tsum) + sumi;
                 sumi = tsum;
             }
         }
