@@ -379,9 +379,9 @@ def paper_flops(cls, info):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
 # kernel class, from an ncu capture of the current kernels at 3D N=64,
 # M=2048, FP32 (warm L2; profiles/fused_pipeline_3d_n64_m2048_fp32.md):
-# k_fused64 1.3 KB + 17.2 KB, k_sep_planes64 0 + 71.4 KB.  Remove an entry
-# when its kernel changes after the capture.
-DRAM_BYTES_3D_N64 = {"pass2": 1280 + 17152, "pass1": 71424}
+# k_fused64 (interleaved unit slots) 0 + 10.2 KB, k_sep_planes64 0 + 71.4 KB.
+# Remove an entry when its kernel changes after the capture.
+DRAM_BYTES_3D_N64 = {"pass2": 0 + 10240, "pass1": 71424}
 
 
 def roofline_of(prof, info, peak32):
