@@ -77,7 +77,9 @@ __device__ __forceinline__ void twiddle_store(cx<T> *tw, cx<T> mine, const cx<T>
 // for FP32 plans, float.
 // 3D: forward transform along axis 1 of every (i1, i3) line, in place (the
 // rows were transformed by k_fwd_rows_2d over all N^2 rows).  A warp holds
-// LPW lines of consecutive i3.
+// LPW lines of consecutive i3.  The rows of a real f are Hermitian in j3, so
+// only the columns j3 = 0 .. N/2 are transformed (N (N/2 + 1) lines); the
+// axis-0 pass writes the other half of the coefficients by symmetry.
 template <int N, typename TC = double>
 __global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
     typedef LineCfg<TC, N> Cfg;
@@ -89,8 +91,9 @@ __global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
+    constexpr int H = N / 2 + 1;
     const int line = blockIdx.x * (blockDim.x / 32) * LPW + wl;
-    const int i1 = line / N, i3 = line - i1 * N;
+    const int i1 = line / H, i3 = line - i1 * H;
     cx<TC> *base = tmp + (size_t)i1 * N * N + i3;
     cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     cx<TC> v[E];
@@ -130,7 +133,10 @@ __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tm
 // Nyquist tables: slice ax holds the modes with j_ax = -N/2 (position N/2),
 // indexed by the other axes in increasing order, with the modes that have an
 // earlier axis at -N/2 set to zero (so the slices are disjoint).
-template <typename TOut, int N, typename TC = double>
+// HALF (3D, after k_fwd_mid_3d): only the columns (j2, j3 <= N/2) are
+// transformed, and each coefficient with 0 < j3 < N/2 also gives its partner
+// ghat(-j) = conj ghat(j) (f is real).
+template <typename TOut, int N, typename TC = double, bool HALF = false>
 __global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict__ ghat,
                            const cx<TC> *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero,
                            cx<TOut> *__restrict__ nslice) {
@@ -143,9 +149,36 @@ __global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % LPW, t = lane / LPW;
     const int wl = warp * LPW + c;
-    const int col = blockIdx.x * (blockDim.x / 32) * LPW + wl;
+    const int line = blockIdx.x * (blockDim.x / 32) * LPW + wl;
     cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     cx<TC> v[E];
+    if constexpr (HALF) {
+        constexpr int H = N / 2 + 1, H2 = N / 2;
+        const int j2 = line / H, j3 = line - j2 * H;
+        const int col = j2 * N + j3;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = tmp[(size_t)(t + e * TPL) * P + col];
+        line_fft<TC, N, E, -1>(v, t, scr, tw);
+        const cx<TOut> zero = mkc<TOut>((TOut)0, (TOut)0);
+        auto emit = [&](int a1, int a2, int a3, cx<TC> x) {
+            if (nyq_zero && (a1 == H2 || a2 == H2 || a3 == H2)) x = mkc<TC>((TC)0, (TC)0);
+            const cx<TOut> val = mkc<TOut>((TOut)(x.x * (TC)inv_nd), (TOut)(x.y * (TC)inv_nd));
+            ghat[(size_t)a1 * P + a2 * N + a3] = val;
+            if (nslice) {
+                if (a1 == H2) nslice[(size_t)a2 * N + a3] = val;
+                if (a2 == H2) nslice[(size_t)N * N + (size_t)a1 * N + a3] = a1 == H2 ? zero : val;
+                if (a3 == H2) nslice[(size_t)2 * N * N + (size_t)a1 * N + a2] = (a1 == H2 || a2 == H2) ? zero : val;
+            }
+        };
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j1 = t + e * TPL;
+            emit(j1, j2, j3, v[e]);
+            if (j3 > 0 && j3 < H2) emit((N - j1) % N, (N - j2) % N, N - j3, mkc<TC>(v[e].x, -v[e].y));
+        }
+        return;
+    }
+    const int col = line;
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = tmp[(size_t)(t + e * TPL) * P + col];
     line_fft<TC, N, E, -1>(v, t, scr, tw);

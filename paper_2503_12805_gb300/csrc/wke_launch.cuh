@@ -89,8 +89,17 @@ static int forward_nc(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
             if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
             k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f),
                                                                                        tmp, tw);
-            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, smem))) return rc;
-            k_fwd_mid_3d<N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
+            // axes 1 and 0 over the Hermitian half j3 <= N/2 (f is real)
+            const int half = N * (N / 2 + 1);
+            const int hw = spread_warps<N>(half);
+            const size_t hsmem = (size_t)(N + hw * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, hsmem))) return rc;
+            k_fwd_mid_3d<N, TC><<<half / (hw * Cfg::LPW), hw * 32, hsmem, s>>>(tmp, tw);
+            if ((rc = set_smem(k_fwd_cols<T, N, TC, true>, hsmem))) return rc;
+            k_fwd_cols<T, N, TC, true><<<half / (hw * Cfg::LPW), hw * 32, hsmem, s>>>(
+                tmp, static_cast<cx<T> *>(hp.dealias ? p.ghat_in : p.ghat), tw, P, hp.d, 1.0 / (double)nd_in(hp),
+                hp.nyquist == WKE_NYQ_ZERO, hp.nyquist == WKE_NYQ_KEEP ? static_cast<cx<T> *>(p.nslice) : nullptr);
+            return (int)cudaGetLastError();
         } else {
             return (int)cudaErrorInvalidValue;
         }
@@ -136,8 +145,11 @@ static int spectrum_n(const HostPlan &hp, const DevicePtrs &p, const void *Q, vo
             if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
             k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(Q),
                                                                                        tmp, tw);
-            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, smem))) return rc;
-            k_fwd_mid_3d<N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, tw);
+            const int half = N * (N / 2 + 1);     // Hermitian half: Q is real
+            const int hw = spread_warps<N>(half);
+            const size_t hsmem = (size_t)(N + hw * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+            if ((rc = set_smem(k_fwd_mid_3d<N, TC>, hsmem))) return rc;
+            k_fwd_mid_3d<N, TC><<<half / (hw * Cfg::LPW), hw * 32, hsmem, s>>>(tmp, tw);
         } else {
             return (int)cudaErrorInvalidValue;
         }
@@ -147,12 +159,23 @@ static int spectrum_n(const HostPlan &hp, const DevicePtrs &p, const void *Q, vo
         if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
         k_fwd_rows_2d<T, N, TC><<<N / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(Q), tmp, tw);
     }
-    const int warps = spread_warps<N>(P);
-    const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
-    if ((rc = set_smem(k_fwd_cols<T, N, TC>, smem))) return rc;
     const size_t nd = (size_t)N * P;
-    k_fwd_cols<T, N, TC><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, static_cast<cx<T> *>(Qhat), tw, P,
-                                                                         hp.d, 1.0 / (double)nd, 0, nullptr);
+    if (hp.d == 3) {
+        if constexpr (N <= 64) {
+            const int half = N * (N / 2 + 1);
+            const int hw = spread_warps<N>(half);
+            const size_t hsmem = (size_t)(N + hw * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+            if ((rc = set_smem(k_fwd_cols<T, N, TC, true>, hsmem))) return rc;
+            k_fwd_cols<T, N, TC, true><<<half / (hw * Cfg::LPW), hw * 32, hsmem, s>>>(
+                tmp, static_cast<cx<T> *>(Qhat), tw, P, hp.d, 1.0 / (double)nd, 0, nullptr);
+        }
+    } else {
+        const int warps = spread_warps<N>(P);
+        const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
+        if ((rc = set_smem(k_fwd_cols<T, N, TC>, smem))) return rc;
+        k_fwd_cols<T, N, TC><<<P / (warps * Cfg::LPW), warps * 32, smem, s>>>(tmp, static_cast<cx<T> *>(Qhat), tw, P,
+                                                                             hp.d, 1.0 / (double)nd, 0, nullptr);
+    }
     const int blocks = (int)std::min<size_t>((nd + 255) / 256, (size_t)num_sms() * 8);
     k_alternate_sign<T><<<blocks, 256, 0, s>>>(static_cast<cx<T> *>(Qhat), hp.d, N, nd);
     return (int)cudaGetLastError();
