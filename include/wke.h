@@ -327,8 +327,9 @@ int wke_plan_autotune(wke_plan *plan, const void *f_dev, void *Q_dev, int reps, 
  * results) with `reps` timed evaluations per launch layout on `stream` (NULL:
  * the plan's own stream), and all but the fastest are destroyed again.  Any
  * other layout value tunes that layout alone.  *out receives the plan (owned
- * by the caller, freed with wke_plan_destroy), layout_out (may be NULL) the
- * layout it uses and best_ms (may be NULL) its milliseconds per evaluation.
+ * by the caller, freed with wke_plan_destroy; a non-NULL `stream` stays its
+ * stream, as after wke_plan_set_stream), layout_out (may be NULL) the layout
+ * it uses and best_ms (may be NULL) its milliseconds per evaluation.
  * Holds at most two plans at a time; synchronises `stream`.  Errors: those of
  * wke_plan_create when no candidate can be built, else those of
  * wke_plan_autotune; *out is NULL after an error. */
