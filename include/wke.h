@@ -62,8 +62,11 @@ extern "C" {
 
 #define WKE_FP64  0   /* every step in double                                 */
 #define WKE_FP32  1   /* transforms and products in float, tables computed in
-                         double and rounded, forward transform and the sum over
-                         quadrature groups in double                           */
+                         double and rounded, forward transform in double; the
+                         sum over chunks of quadrature groups in a compensated
+                         float pair (hi + lo, about twice the float
+                         significand) in the fused kernels, in double
+                         otherwise                                             */
 #define WKE_SPLIT 2   /* WKE_FP32 (float data) whose axis-0 transforms run on
                          the tensor cores: each N-point DFT as a real GEMM in
                          TF32 with both operands split into a TF32 high part
