@@ -105,8 +105,13 @@ __global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict_
 }
 
 // Forward transform of every row (the last axis): the N rows of a 2D grid,
-// or the N^2 rows of a 3D one.
-template <typename TIn, int N, typename TC = double>
+// or the N^2 rows of a 3D one.  PACK: each line transforms two real rows at
+// once, Z = DFT(f_a + i f_b), and separates them with the partner value
+// Z(N - j) from the lane holding it (f_a and f_b are real, so
+// F_a(j) = (Z(j) + conj Z(N - j)) / 2 and F_b(j) = (Z(j) - conj Z(N - j)) / 2i):
+// half the transforms.  Thread t of a line holds j = t + e TPL, so Z(N - j)
+// sits in thread TPL - t at e' = E - 1 - e (thread 0: itself, e' = E - e mod E).
+template <typename TIn, int N, typename TC = double, bool PACK = false>
 __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
     typedef LineCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
@@ -120,6 +125,31 @@ __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tm
     const int i1 = blockIdx.x * (blockDim.x / 32) * LPW + wl;
     cx<TC> *scr = scratch + (size_t)wl * LinePad<N>::PITCH;
     cx<TC> v[E];
+    if constexpr (PACK) {
+        const size_t ra = (size_t)(2 * i1) * N, rb = ra + N;     // rows 2 i1 and 2 i1 + 1
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = mkc<TC>((TC)f[ra + t + e * TPL], (TC)f[rb + t + e * TPL]);
+        line_fft<TC, N, E, -1>(v, t, scr, tw);
+        const int partner = ((TPL - t) % TPL) * LPW + c;
+        cx<TC> zr[E];   // Z(N - j) for this thread's j = t + e TPL
+#pragma unroll
+        for (int es = 0; es < E; ++es) {
+            const cx<TC> w = mkc<TC>(__shfl_sync(0xffffffffu, v[es].x, partner),
+                                     __shfl_sync(0xffffffffu, v[es].y, partner));
+            if (t == 0)
+                zr[(E - es) % E] = w;
+            else
+                zr[E - 1 - es] = w;
+        }
+        const TC h = (TC)0.5;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const cx<TC> z = v[e], m = zr[e];
+            tmp[ra + t + e * TPL] = mkc<TC>(h * (z.x + m.x), h * (z.y - m.y));
+            tmp[rb + t + e * TPL] = mkc<TC>(h * (z.y + m.y), h * (m.x - z.x));
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = mkc<TC>((TC)f[(size_t)i1 * N + t + e * TPL], (TC)0);
     line_fft<TC, N, E, -1>(v, t, scr, tw);

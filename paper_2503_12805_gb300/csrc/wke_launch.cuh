@@ -81,14 +81,15 @@ static int forward_nc(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
-            // rows (axis 2) of all N^2 rows, then axis 1 of all N^2 lines: line
-            // kernels over the whole grid, so every SM takes part in the FP64 work
-            const int rows = N * N;
+            // rows (axis 2) of all N^2 rows, two real rows per transform, then
+            // axes 1 and 0: line kernels over the whole grid, so every SM takes
+            // part in the FP64 work
+            const int rows = N * N / 2;
             const int warps = spread_warps<N>(rows);
             const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
-            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
-            k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(p.f),
-                                                                                       tmp, tw);
+            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC, true>, smem))) return rc;
+            k_fwd_rows_2d<T, N, TC, true><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(
+                static_cast<const T *>(p.f), tmp, tw);
             // axes 1 and 0 over the Hermitian half j3 <= N/2 (f is real)
             const int half = N * (N / 2 + 1);
             const int hw = spread_warps<N>(half);
@@ -139,12 +140,13 @@ static int spectrum_n(const HostPlan &hp, const DevicePtrs &p, const void *Q, vo
     int rc = 0;
     if (hp.d == 3) {
         if constexpr (N <= 64) {
-            const int rows = N * N;
+            // rows (axis 2) two real rows per transform
+            const int rows = N * N / 2;
             const int warps = spread_warps<N>(rows);
             const size_t smem = (size_t)(N + warps * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
-            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC>, smem))) return rc;
-            k_fwd_rows_2d<T, N, TC><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(static_cast<const T *>(Q),
-                                                                                       tmp, tw);
+            if ((rc = set_smem(k_fwd_rows_2d<T, N, TC, true>, smem))) return rc;
+            k_fwd_rows_2d<T, N, TC, true><<<rows / (warps * Cfg::LPW), warps * 32, smem, s>>>(
+                static_cast<const T *>(Q), tmp, tw);
             const int half = N * (N / 2 + 1);     // Hermitian half: Q is real
             const int hw = spread_warps<N>(half);
             const size_t hsmem = (size_t)(N + hw * Cfg::LPW * LinePad<N>::PITCH) * sizeof(cx<TC>);
