@@ -601,7 +601,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config("fp64 (CPU oracle)"),
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": workers, "kind": "oracle",
-                             "sample": f"{args.steps} whole evaluations, one per step, node ranges over "
+                             "sample": f"{args.steps} whole evaluation{'s' if args.steps != 1 else ''}, one per step, node ranges over "
                                        f"{workers} spawn processes; {wall:.1f} s wall"},
             "e2e": {"value": round(rate, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
