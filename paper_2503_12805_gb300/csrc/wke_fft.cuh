@@ -299,6 +299,16 @@ template <typename T, int N> struct LineCfg {
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
 };
 
+// Points per thread of the forward transform's line kernels: 4 at N = 64 (16
+// threads per line, radices 4, 4, 4: twice the warps of LineCfg, since these
+// passes have only N^2 / 2 to N^2 lines for the whole GPU), else LineCfg's.
+template <typename T, int N> struct FwdCfg {
+    static constexpr int E = N == 64 ? 4 : LineCfg<T, N>::E;
+    static constexpr int TPL = N / E;
+    static constexpr int LPW = 32 / TPL;
+    static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
+};
+
 // 64-point inverse line transform of 4 lines per warp (lane = c + 4 t, thread
 // t of line c holds x[t + 8 e] in v[e] and returns X[t + 8 e]): a radix-8
 // DFT over e in registers, the twiddles w64^{t k1} (wt, per thread), an

@@ -82,7 +82,7 @@ __device__ __forceinline__ void twiddle_store(cx<T> *tw, cx<T> mine, const cx<T>
 // axis-0 pass writes the other half of the coefficients by symmetry.
 template <int N, typename TC = double>
 __global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
-    typedef LineCfg<TC, N> Cfg;
+    typedef FwdCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);
@@ -113,7 +113,7 @@ __global__ void k_fwd_mid_3d(cx<TC> *__restrict__ tmp, const cx<TC> *__restrict_
 // sits in thread TPL - t at e' = E - 1 - e (thread 0: itself, e' = E - e mod E).
 template <typename TIn, int N, typename TC = double, bool PACK = false>
 __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tmp, const cx<TC> *__restrict__ tw_g) {
-    typedef LineCfg<TC, N> Cfg;
+    typedef FwdCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);
@@ -170,7 +170,7 @@ template <typename TOut, int N, typename TC = double, bool HALF = false>
 __global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict__ ghat,
                            const cx<TC> *__restrict__ tw_g, int P, int d, double inv_nd, int nyq_zero,
                            cx<TOut> *__restrict__ nslice) {
-    typedef LineCfg<TC, N> Cfg;
+    typedef FwdCfg<TC, N> Cfg;
     constexpr int E = Cfg::E, TPL = Cfg::TPL, LPW = Cfg::LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<TC> *tw = reinterpret_cast<cx<TC> *>(smem_raw);

@@ -58,7 +58,7 @@ template <typename T, int N> static int line_warps(int lines) {
 // largest power of two up to KCfg::WARPS that keeps at least one block per SM
 // and divides the lines, since FP64 line work is bound by each SM's FP64 units.
 template <int N> static int spread_warps(int lines) {
-    typedef LineCfg<double, N> Cfg;
+    typedef FwdCfg<double, N> Cfg;   // the forward transform's line kernels
     int warps = 1;
     while (2 * warps <= KCfg<double>::WARPS && lines % (2 * warps * Cfg::LPW) == 0 &&
            lines / (2 * warps * Cfg::LPW) >= num_sms())
@@ -74,7 +74,7 @@ template <int N> static int spread_warps(int lines) {
 // for FP32 plans that are not de-aliased, with the plan's float twiddles).
 template <typename T, int N, typename TC>
 static int forward_nc(const HostPlan &hp, const DevicePtrs &p, cudaStream_t s) {
-    typedef LineCfg<TC, N> Cfg;
+    typedef FwdCfg<TC, N> Cfg;
     const int P = hp.d == 2 ? N : N * N;
     cx<TC> *tmp = static_cast<cx<TC> *>(p.fwd_tmp);
     const cx<TC> *tw = sizeof(TC) == 8 ? reinterpret_cast<const cx<TC> *>(p.tw64) : static_cast<const cx<TC> *>(p.tw);
@@ -133,7 +133,7 @@ template <typename T, int N> static int forward_n(const HostPlan &hp, const Devi
 template <typename T, int N>
 static int spectrum_n(const HostPlan &hp, const DevicePtrs &p, const void *Q, void *Qhat, cudaStream_t s) {
     typedef double TC;
-    typedef LineCfg<TC, N> Cfg;
+    typedef FwdCfg<TC, N> Cfg;
     const int P = hp.d == 2 ? N : N * N;
     cx<TC> *tmp = static_cast<cx<TC> *>(p.fwd_tmp);
     const cx<TC> *tw = reinterpret_cast<const cx<TC> *>(p.tw64);
