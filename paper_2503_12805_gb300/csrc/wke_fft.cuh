@@ -299,11 +299,11 @@ template <typename T, int N> struct LineCfg {
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
 };
 
-// Points per thread of the forward transform's line kernels: 4 at N = 64 (16
-// threads per line, radices 4, 4, 4: twice the warps of LineCfg, since these
+// Points per thread of the forward transform's line kernels: 2 at N = 64 (a
+// warp per line, radix-2 stages: four times the warps of LineCfg, since these
 // passes have only N^2 / 2 to N^2 lines for the whole GPU), else LineCfg's.
 template <typename T, int N> struct FwdCfg {
-    static constexpr int E = N == 64 ? 4 : LineCfg<T, N>::E;
+    static constexpr int E = N == 64 ? 2 : LineCfg<T, N>::E;
     static constexpr int TPL = N / E;
     static constexpr int LPW = 32 / TPL;
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");

@@ -148,13 +148,13 @@ __global__ void k_fwd_rows_2d(const TIn *__restrict__ f, cx<TC> *__restrict__ tm
             tmp[ra + t + e * TPL] = mkc<TC>(h * (z.x + m.x), h * (z.y - m.y));
             tmp[rb + t + e * TPL] = mkc<TC>(h * (z.y + m.y), h * (m.x - z.x));
         }
-        return;
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = mkc<TC>((TC)f[(size_t)i1 * N + t + e * TPL], (TC)0);
+        line_fft<TC, N, E, -1>(v, t, scr, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) tmp[(size_t)i1 * N + t + e * TPL] = v[e];
     }
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = mkc<TC>((TC)f[(size_t)i1 * N + t + e * TPL], (TC)0);
-    line_fft<TC, N, E, -1>(v, t, scr, tw);
-#pragma unroll
-    for (int e = 0; e < E; ++e) tmp[(size_t)i1 * N + t + e * TPL] = v[e];
 }
 
 // Both d: forward transform along axis 0 of every column; writes
@@ -206,38 +206,38 @@ __global__ void k_fwd_cols(const cx<TC> *__restrict__ tmp, cx<TOut> *__restrict_
             emit(j1, j2, j3, v[e]);
             if (j3 > 0 && j3 < H2) emit((N - j1) % N, (N - j2) % N, N - j3, mkc<TC>(v[e].x, -v[e].y));
         }
-        return;
-    }
-    const int col = line;
+    } else {
+        const int col = line;
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = tmp[(size_t)(t + e * TPL) * P + col];
-    line_fft<TC, N, E, -1>(v, t, scr, tw);
-    bool col_nyq = false;
-    if (nyq_zero) {
-        int rest = col;
-        for (int a = 1; a < d; ++a) {
-            if (rest % N == N / 2) col_nyq = true;
-            rest /= N;
+        for (int e = 0; e < E; ++e) v[e] = tmp[(size_t)(t + e * TPL) * P + col];
+        line_fft<TC, N, E, -1>(v, t, scr, tw);
+        bool col_nyq = false;
+        if (nyq_zero) {
+            int rest = col;
+            for (int a = 1; a < d; ++a) {
+                if (rest % N == N / 2) col_nyq = true;
+                rest /= N;
+            }
         }
-    }
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int j1 = t + e * TPL;
-        cx<TC> x = v[e];
-        if (nyq_zero && (col_nyq || j1 == N / 2)) x = mkc<TC>((TC)0, (TC)0);
-        const cx<TOut> val = mkc<TOut>((TOut)(x.x * (TC)inv_nd), (TOut)(x.y * (TC)inv_nd));
-        ghat[(size_t)j1 * P + col] = val;
-        if (nslice) {
-            const cx<TOut> zero = mkc<TOut>((TOut)0, (TOut)0);
-            constexpr int H2 = N / 2;
-            if (d == 3) {
-                const int j2 = col / N, j3 = col - j2 * N;
-                if (j1 == H2) nslice[(size_t)j2 * N + j3] = val;
-                if (j2 == H2) nslice[(size_t)N * N + (size_t)j1 * N + j3] = j1 == H2 ? zero : val;
-                if (j3 == H2) nslice[(size_t)2 * N * N + (size_t)j1 * N + j2] = (j1 == H2 || j2 == H2) ? zero : val;
-            } else {
-                if (j1 == H2) nslice[col] = val;
-                if (col == H2) nslice[N + j1] = j1 == H2 ? zero : val;
+        for (int e = 0; e < E; ++e) {
+            const int j1 = t + e * TPL;
+            cx<TC> x = v[e];
+            if (nyq_zero && (col_nyq || j1 == N / 2)) x = mkc<TC>((TC)0, (TC)0);
+            const cx<TOut> val = mkc<TOut>((TOut)(x.x * (TC)inv_nd), (TOut)(x.y * (TC)inv_nd));
+            ghat[(size_t)j1 * P + col] = val;
+            if (nslice) {
+                const cx<TOut> zero = mkc<TOut>((TOut)0, (TOut)0);
+                constexpr int H2 = N / 2;
+                if (d == 3) {
+                    const int j2 = col / N, j3 = col - j2 * N;
+                    if (j1 == H2) nslice[(size_t)j2 * N + j3] = val;
+                    if (j2 == H2) nslice[(size_t)N * N + (size_t)j1 * N + j3] = j1 == H2 ? zero : val;
+                    if (j3 == H2) nslice[(size_t)2 * N * N + (size_t)j1 * N + j2] = (j1 == H2 || j2 == H2) ? zero : val;
+                } else {
+                    if (j1 == H2) nslice[col] = val;
+                    if (col == H2) nslice[N + j1] = j1 == H2 ? zero : val;
+                }
             }
         }
     }
@@ -504,8 +504,8 @@ k_sep_planes64(const float2 *__restrict__ ghat, const float2 *__restrict__ phase
     __syncthreads();
     const size_t NN = (size_t)N * N;
     for (int p = pb; p < pe; ++p) {
-        const int pf = sep_p[p0 + p];
-        if (!WKE_GUARD(pf >= 0 && pf < n_fields, kChkSepPair)) continue;
+        // (checked builds: the pair's field, whose phase row was staged)
+        if (!WKE_GUARD(sep_p[p0 + p] >= 0 && sep_p[p0 + p] < n_fields, kChkSepPair)) continue;
         const float2 *e1 = eph + (1 + p - pb) * N;
         // column-blocked plane (sep_col64): this warp's 4 columns are one
         // contiguous 64 x 4 block, so each store instruction writes 256 bytes
