@@ -512,10 +512,37 @@ def _serving_initial(d, N, seed):
     return I.ring(3, N, 8.0) if seed % 2 else I.gaussian_noise(3, N, 8.0, seed)
 
 
-def run_stream(n_requests, seed, rate, wke, budget_bytes, max_active):
+def shape_step_ms(wke, seed):
+    """Milliseconds of one FP32 RK4 step (dt = 1e-3) of every request shape
+    of the mix, each run alone on the GPU (CUDA events, 2 warm-up and 5 timed
+    steps; the plans the server would build)."""
+    import torch
+    out = {}
+    for d, N, n_r, n_s, n_sig in serving_mix():
+        plan = wke.Plan(d, N, 8.0, n_r, n_s, n_sig, precision="fp32")
+        f0 = torch.tensor(_serving_initial(d, N, seed), dtype=torch.float32, device="cuda")
+        f = f0.clone()
+        for _ in range(2):
+            plan.step(f, 1e-3, 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f.copy_(f0)
+        e0.record()
+        for _ in range(5):
+            plan.step(f, 1e-3, 4)
+        e1.record()
+        torch.cuda.synchronize()
+        out[(d, N)] = e0.elapsed_time(e1) / 5
+        plan.close()
+    return out
+
+
+def run_stream(n_requests, seed, rate, wke, budget_bytes, max_active, step_ms=None):
     """A seeded Poisson stream at `rate` req/s of mixed requests (1-20 RK4
     steps, dt = 1e-3, FP32) through the continuous-batching server; latency
-    is completion minus submission on the server's clock."""
+    is completion minus submission on the server's clock.  With `step_ms`
+    (shape_step_ms) it also reports the stream's serial GPU time: every
+    request's steps timed alone and added up, over the stream's wall time,
+    and the share of that time in 2D requests."""
     import numpy as np
     sizes = serving_mix()
     u = I.splitmix64_uniform(seed, 3 * n_requests)
@@ -549,20 +576,27 @@ def run_stream(n_requests, seed, rate, wke, budget_bytes, max_active):
     wait = np.array([st.t_admit - st.t_submit for st in ok]) * 1000.0
     span = max(st.t_done for st in ok) - min(st.t_submit for st in ok)
     evals = sum(4 * r[5] for r in reqs)
-    return {"offered_req_s": rate, "requests": n_requests, "completed": len(ok),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "admission_wait_p50_ms": round(float(np.percentile(wait, 50)), 3),
-            "served_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2)}
+    out = {"offered_req_s": rate, "requests": n_requests, "completed": len(ok),
+           "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "admission_wait_p50_ms": round(float(np.percentile(wait, 50)), 3),
+           "served_req_s": round(len(ok) / span, 3), "q_evals_per_s": round(evals / span, 2)}
+    if step_ms:
+        serial = [r[5] * step_ms[(r[0], r[1])] for r in reqs]
+        out["serial_gpu_s_over_wall"] = round(sum(serial) / 1000.0 / span, 3)
+        out["serial_share_2d"] = round(sum(t for t, r in zip(serial, reqs) if r[0] == 2) / sum(serial), 4)
+    return out
 
 
 def run_serving(n_requests, seed, wke, budget_bytes, max_active):
     """Latency and throughput of the mixed stream at offered loads below and
     at saturation (SWEEP_RATES) and at the configured SERVE_RATE; the served
     rate at SERVE_RATE is the saturation throughput."""
-    sweep = [run_stream(n_requests, seed + 1000 * i, rate, wke, budget_bytes, max_active)
+    step_ms = shape_step_ms(wke, seed)
+    sweep = [run_stream(n_requests, seed + 1000 * i, rate, wke, budget_bytes, max_active, step_ms)
              for i, rate in enumerate(SWEEP_RATES)]
-    cfg = run_stream(n_requests, seed, SERVE_RATE, wke, budget_bytes, max_active)
+    cfg = run_stream(n_requests, seed, SERVE_RATE, wke, budget_bytes, max_active, step_ms)
     return {"sweep": sweep, "configured": cfg, "saturation_req_s": cfg["served_req_s"],
+            "rk4_step_ms_alone": {f"{d}d_n{N}": round(v, 4) for (d, N), v in step_ms.items()},
             "max_active": max_active, "budget_gib": round(budget_bytes / 2 ** 30, 1),
             "latency": "submission to completion on the server clock; one plan of every shape created before "
                        "each stream",
