@@ -231,7 +231,14 @@ static int build_shared_layout(HostPlan &hp, bool force) {
         }
         return (int)seen.size();
     };
-    auto fits = [&](int K) { return K <= kMaxChunkFields && (size_t)((K + 1) / 2) <= max_units; };
+    // 3D FP32 (not split): a chunk's fields must also fit the shared memory of
+    // the fused axis-0 + product kernel, so that the plan can use it (at
+    // N = 48 two radii of the cube rule instead of three)
+    const bool fusable = d == 3 && hp.precision == WKE_FP32 && !hp.split;
+    auto fits = [&](int K) {
+        return K <= kMaxChunkFields && (size_t)((K + 1) / 2) <= max_units &&
+               (!fusable || fused_smem_bytes(hp.N, K) <= 227 * 1024);
+    };
     // Chunk boundaries: whole radial shells (the n_s groups of one radius,
     // which share most fields) while they fit; a shell too large alone is
     // split group by group.
