@@ -299,11 +299,12 @@ template <typename T, int N> struct LineCfg {
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
 };
 
-// Points per thread of the forward transform's line kernels: 2 at N = 64 (a
-// warp per line, radix-2 stages: four times the warps of LineCfg, since these
-// passes have only N^2 / 2 to N^2 lines for the whole GPU), else LineCfg's.
+// Points per thread of the forward transform's line kernels: 2 at N = 32 and
+// 64 (radix-2 stages), 6 at N = 48 (a radix-3 stage, then radix 2): more
+// threads per line than LineCfg (four times the warps at N = 64), since these
+// passes have only N^2 / 2 to N^2 lines for the whole GPU; LineCfg's otherwise.
 template <typename T, int N> struct FwdCfg {
-    static constexpr int E = N == 64 ? 2 : LineCfg<T, N>::E;
+    static constexpr int E = (N == 32 || N == 64) ? 2 : N == 48 ? 6 : LineCfg<T, N>::E;
     static constexpr int TPL = N / E;
     static constexpr int LPW = 32 / TPL;
     static_assert(TPL >= 1 && TPL <= 32, "line must fit one warp");
