@@ -49,7 +49,7 @@ extern "C" {
 #define WKE_ERR_INVALID       -1   /* bad argument (sizes, rule, pointers)   */
 #define WKE_ERR_OOM           -2   /* device or host allocation failed        */
 #define WKE_ERR_CUDA          -3   /* a CUDA runtime call or launch failed    */
-#define WKE_ERR_UNSUPPORTED   -4   /* valid request this build does not serve */
+#define WKE_ERR_UNSUPPORTED   -4   /* valid request the library has no kernel for */
 #define WKE_CANCELLED         -5   /* a served request was cancelled before it ran */
 
 /* ------------------------------------------------------------ enumerations */

@@ -144,7 +144,7 @@ def headline_reference():
     return f, ref
 
 
-# The headline workload is held to the benchmark spec's figures over the whole grid:
+# The headline workload is held to its target tolerances over the whole grid:
 # FP64 1e-12, and 1e-6 for both the FP32 path and the split-precision path.
 HEADLINE_TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-6}
 
