@@ -174,6 +174,42 @@ def test_shared_field_layout_counts(wke):
     assert two_d.shared_fields == 1 and two_d.products_per_group == 1 and two_d.units_per_collision == 32 * 4
 
 
+def test_fp32_chunks_fit_the_fused_kernel(wke):
+    """3D FP32 plans chunk so that the fused axis-0 + product kernel holds a
+    chunk's fields: at N = 48 (the 24 x 8 x 8 cube rule of the serving mix)
+    two radii per chunk (52 fields) instead of three (78 fields, more shared
+    memory than a block has), so the plan fuses; N = 32 keeps three radii and
+    N = 64 one, and FP64 plans (no fused kernel) keep their own chunking."""
+    n48 = _describe(wke, 3, 48, 24, 8, 8, precision=wke.WKE_FP32)
+    assert n48.fused_products == 1 and n48.n_chunks == 12 and n48.groups_per_chunk == 16
+    n32 = _describe(wke, 3, 32, 16, 8, 8, precision=wke.WKE_FP32)
+    assert n32.fused_products == 1 and n32.n_chunks == 6 and n32.groups_per_chunk == 24
+    n64 = _describe(wke, 3, 64, 32, 8, 8, precision=wke.WKE_FP32)
+    assert n64.fused_products == 1 and n64.n_chunks == 32
+    f64 = _describe(wke, 3, 48, 24, 8, 8, precision=wke.WKE_FP64)
+    assert f64.fused_products == 0 and f64.n_chunks == 24
+
+
+def test_autotuned_creation_checks_arguments_before_device_work(wke):
+    """wke_plan_create_autotuned refuses a NULL out, a NULL f or Q, reps < 1
+    and an invalid plan (M != n_r n_s n_sig) with WKE_ERR_INVALID before it
+    creates any plan or touches a device; *out stays NULL."""
+    q = wke.wke_quadrature_default()
+    q.n_r, q.n_s, q.n_sig = 2, 4, 4
+    out = ctypes.c_void_p(1)
+    fake = ctypes.c_void_p(16)        # never dereferenced on these paths
+    lib = wke.lib()
+    assert lib.wke_plan_create_autotuned(2, 16, 8.0, 32, ctypes.byref(q), fake, fake, None, 1, None, None,
+                                         None) == wke.WKE_ERR_INVALID
+    for f_ptr, q_ptr, reps, M in ((None, fake, 1, 32), (fake, None, 1, 32), (fake, fake, 0, 32),
+                                  (fake, fake, 1, 33)):
+        out.value = 1
+        rc = lib.wke_plan_create_autotuned(2, 16, 8.0, M, ctypes.byref(q), f_ptr, q_ptr, None, reps,
+                                           ctypes.byref(out), None, None)
+        assert rc == wke.WKE_ERR_INVALID and not out.value
+        assert lib.wke_last_error_string()
+
+
 def test_describe_matches_footprint_and_rejects_like_create(wke):
     q = wke.wke_quadrature_default()
     q.n_r, q.n_s, q.n_sig = 4, 8, 8
